@@ -1,0 +1,177 @@
+/*
+ * C ABI of the GB300 correlator library (libcorr.so).
+ *
+ * The operation is the X-step of an FX correlator as stated in Section 2 of
+ * van Nieuwpoort & Romein, "Correlating Radio Astronomy Signals with
+ * Many-Core Hardware": for every frequency channel, every pair of stations
+ * s1 <= s2 (autocorrelations included) and every pair of polarisations
+ * p1, p2 in {X, Y},
+ *
+ *     V[ch][baseline(s1,s2)][p1][p2] = sum_t  x[ch][s1][t][p1] * conj(x[ch][s2][t][p2]),
+ *
+ * with baseline(s1, s2) = s2*(s2+1)/2 + s1 (the order the loop nest of Fig. 2
+ * visits the pairs). There are S(S+1)/2 baselines per channel.
+ *
+ * Memory layouts (all complex values are (re, im) interleaved):
+ *   input  : [integration][channel][station][time][pol]
+ *            CORR_CF32 -> 2 x float32, CORR_CF16 -> 2 x float16,
+ *            CORR_CI8  -> 2 x int8
+ *   output : [integration][channel][baseline][pol1][pol2]
+ *            complex float32 for CORR_CF32 / CORR_CF16 inputs,
+ *            complex int32 for CORR_CI8 inputs (bit-exact).
+ *   gains  : [integration][channel][station][pol], complex float32.
+ *
+ * Ownership: the caller owns every buffer passed in; all pointers named d_*
+ * are device pointers on the plan's device and must be 16-byte aligned.
+ * The plan owns its work lists, error word and workspaces; it allocates
+ * device memory only in corr_create and on the first call of
+ * corr_correlate_batched with a new set of sub-arrays.
+ *
+ * Calls are asynchronous on the given stream (a cudaStream_t passed as
+ * void*, NULL = legacy default stream) and do not synchronize, except where
+ * stated. Argument errors are detected on the host before any launch and
+ * returned as status codes; nothing aborts or exits. A kernel that gives up
+ * waiting on an internal pipeline barrier sets the plan's error word, which
+ * corr_get_error reports as CORR_ERR_TIMEOUT.
+ *
+ * Only two polarisations are supported (n_pols must be 2, as in the paper).
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct corr_plan *corr_handle_t;
+
+typedef enum {
+    CORR_OK = 0,
+    CORR_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or handle */
+    CORR_ERR_UNSUPPORTED = 2, /* valid request this library does not implement */
+    CORR_ERR_NO_MEMORY = 3,   /* device or host allocation failed */
+    CORR_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    CORR_ERR_TIMEOUT = 5      /* a kernel gave up on a pipeline wait */
+} corr_status_t;
+
+typedef enum { CORR_CF32 = 0, CORR_CF16 = 1, CORR_CI8 = 2 } corr_dtype_t;
+
+/* Which kernel family computes the products.
+ *   CORR_PATH_FP32   : FP32 CUDA-core kernel (4 FMAs per complex multiply-add,
+ *                      Section 2); inputs CORR_CF32 only.
+ *   CORR_PATH_TENSOR : tcgen05 tensor-core kernel; CORR_CF16 (FP32
+ *                      accumulation) or CORR_CI8 (exact, INT32 result).
+ *   CORR_PATH_AUTO   : FP32 for CORR_CF32, TENSOR otherwise. */
+typedef enum { CORR_PATH_AUTO = 0, CORR_PATH_FP32 = 1, CORR_PATH_TENSOR = 2 } corr_path_t;
+
+/* Plan flags. */
+#define CORR_FLAG_GAINS 0x1u      /* allocate the gain-calibration workspace */
+#define CORR_FLAG_NO_AUTOTUNE 0x2u /* skip timed tile selection at create */
+
+typedef struct {
+    int n_stations;     /* S >= 1                                   (Section 2) */
+    int n_pols;         /* must be 2 (X and Y)                      (Section 2) */
+    int n_channels;     /* C >= 1                                   (Section 2) */
+    int n_samples;      /* T >= 0, samples per integration          (Section 2) */
+    int n_integrations; /* >= 1, integrations stacked before channels           */
+    int dtype;          /* corr_dtype_t of the input samples                     */
+    int path;           /* corr_path_t                                            */
+    unsigned flags;     /* CORR_FLAG_*                                            */
+} corr_desc_t;
+
+/* One sub-array of a ragged batch: its own S, C, T, input and output
+ * (layouts as above with one integration). */
+typedef struct {
+    int n_stations;
+    int n_channels;
+    int n_samples;
+    int reserved; /* must be 0 */
+    const void *d_in;
+    void *d_out;
+} corr_subarray_t;
+
+/* Creates a plan for the problem described by *desc on the current CUDA
+ * device. Validates the description, allocates the plan's device work list
+ * and error word, and (unless CORR_FLAG_NO_AUTOTUNE) times the candidate tile
+ * shapes once for this shape (this synchronizes the device). On success
+ * *out receives the handle; on failure *out is set to NULL. */
+corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out);
+
+/* Correlates all integrations and channels of the plan (Section 2, the
+ * correlation formula; Fig. 2). d_in: input samples, layout and type as
+ * above, n_integrations*n_channels*n_stations*n_samples*2 complex values;
+ * d_out: visibilities, n_integrations*n_channels*S(S+1)/2*4 complex values,
+ * fully overwritten. Asynchronous on stream; capturable in a CUDA graph. */
+corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream);
+
+/* Correlates a ragged batch of n_sub independent sub-arrays (each with its
+ * own S, C and T, channels independent as in Section 2) in one persistent
+ * kernel launch on the tensor path with the plan's dtype (CORR_CF16 or
+ * CORR_CI8). The plan's own S, C and T are ignored. The first call with a
+ * new set of sub-arrays (shapes or pointers) builds and uploads the work
+ * list and synchronizes; it must not be captured. Later calls with the same
+ * set only launch and are capturable. */
+corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_subarray_t *subs,
+                                     void *stream);
+
+/* Gain-calibration loss (not in the paper; the calibration step that
+ * consumes the autocorrelations is named in Section 2). With raw
+ * visibilities R = corr(x) from corr_correlate, gains g and model M:
+ *     V_ab = g_a conj(g_b) R_ab,   L = sum |V_ab - M_ab|^2
+ * over channels, baselines and pol pairs. d_raw_vis, d_vis_model: complex
+ * float32 [units][B][2][2]; d_gain: complex float32 [units][S][2];
+ * d_vis_out (nullable) receives V; d_loss (nullable) receives L (float32).
+ * Requires a plan created with CORR_FLAG_GAINS and dtype CORR_CF32. */
+corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
+                             const void *d_vis_model, void *d_vis_out, float *d_loss,
+                             void *stream);
+
+/* Adjoint of corr_gain_loss: gradients in the PyTorch convention for a real
+ * loss of complex inputs (dL/dRe + i dL/dIm = 2 dL/d conj(z)), scaled by
+ * *d_grad_scale (device float, nullable = 1).
+ *   d_grad_gain (required): [units][S][2] complex float32,
+ *       dL/d conj(g_c) = sum_(c,b) E_cb g_b conj(R_cb) + sum_(a,c) conj(E_ac) g_a R_ac;
+ *   d_grad_in (nullable): same layout as d_in (complex float32),
+ *       dL/d conj(x_c(t)) = conj(g_c) sum_b W_cb g_b x_b(t),
+ *       W_cb = [s_c<=s_b] E_cb + [s_b<=s_c] conj(E_bc), E = V - M;
+ *   d_raw_vis (nullable): R from a previous corr_correlate; recomputed if NULL;
+ *   d_loss (nullable): receives L. */
+corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *d_gain,
+                                 const void *d_vis_model, const void *d_raw_vis,
+                                 void *d_grad_gain, void *d_grad_in, float *d_loss,
+                                 const float *d_grad_scale, void *stream);
+
+/* Frees the plan and its device memory (synchronizes the plan's device).
+ * NULL is accepted. */
+corr_status_t corr_destroy(corr_handle_t h);
+
+/* Reads and clears the plan's device error word (synchronous copy):
+ * CORR_OK or CORR_ERR_TIMEOUT. */
+corr_status_t corr_get_error(corr_handle_t h);
+
+/* Static description of a status code. */
+const char *corr_status_string(corr_status_t s);
+
+/* Host-only helpers (no GPU needed), used by the plan and by tests. */
+
+/* Tile cost model of Section 2 (Table 1) for a w x h station tile:
+ * flops = 32wh, bytes = 16(w+h), minimum registers = 4(1+min(w,h)) + 8wh. */
+void corr_tile_cost(int w, int h, long *flops, long *bytes, long *regs);
+
+/* Number of tensor-path work tiles for S stations (upper triangle of
+ * 64-station blocks, diagonal included) and the decode of tile k into its
+ * row and column block (rb <= cb). Returns -1 for k out of range. */
+int corr_tc_tiles(int n_stations);
+int corr_tc_tile_decode(int n_stations, int k, int *rb, int *cb);
+
+/* Number of 4x4-station register tiles of the FP32 path per channel
+ * (upper triangle, diagonal included) and the decode of tile k into its
+ * row and column index (i <= j). Returns -1 for k out of range. */
+int corr_fp32_subtiles(int n_stations);
+int corr_fp32_subtile_decode(int n_stations, int k, int *i, int *j);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

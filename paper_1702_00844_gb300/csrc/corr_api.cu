@@ -1,0 +1,448 @@
+// C ABI of the correlator: plan creation, argument checks, work lists and
+// kernel dispatch. See include/corr.h for the contract of every entry point.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/corr.h"
+#include "corr_internal.h"
+
+using namespace corr;
+
+struct corr_plan {
+    corr_desc_t d{};
+    int device = 0;
+    int sm_count = 0;
+    int path = CORR_PATH_FP32;
+    int *d_err = nullptr;
+    unsigned long long wait_ns = 2000000000ull;
+    // FP32 path
+    Fp32Params fp{};
+    int fp_threads = 0;
+    size_t fp_smem = 0;
+    // tensor path (single problem)
+    int4 *d_items = nullptr;
+    int n_items = 0;
+    int tc_grid = 0;
+    // ragged batches
+    std::vector<corr_subarray_t> batch_key;
+    TcProblem *d_bprobs = nullptr;
+    int4 *d_bitems = nullptr;
+    int n_bitems = 0;
+    // gain calibration
+    float2 *d_R = nullptr;     // recomputed raw visibilities
+    float2 *d_W = nullptr;     // W' per channel
+    float *d_partial = nullptr;
+};
+
+namespace {
+
+constexpr int TC_SIDE = TC_RS;
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+long long n_baselines(long long S) { return S * (S + 1) / 2; }
+
+int tc_blocks(int S) { return (S + TC_SIDE - 1) / TC_SIDE; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// FP32 input as a 4-D tensor: (4 floats of one station and time) x station x
+// time x unit, boxes of 4 x 8 stations x tc samples x 1 unit, so that a box
+// lands in shared memory as [t][8 stations][4 floats].
+corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, int units, int tc)
+{
+    auto fn = encode_fn();
+    if (!fn) return CORR_ERR_CUDA;
+    cuuint64_t dims[4] = {4, (cuuint64_t)S, (cuuint64_t)T, (cuuint64_t)units};
+    cuuint64_t strides[3] = {(cuuint64_t)T * 16, 16, (cuuint64_t)S * T * 16};
+    cuuint32_t box[4] = {4, 8, (cuuint32_t)tc, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(d_in), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CORR_OK : CORR_ERR_CUDA;
+}
+
+void fp32_config(corr_plan *h)
+{
+    const int S = h->d.n_stations;
+    Fp32Params &p = h->fp;
+    p.S = S;
+    p.T = h->d.n_samples;
+    p.n_units = h->d.n_channels * h->d.n_integrations;
+    p.nq = (S + 3) / 4;
+    p.nsub = p.nq * (p.nq + 1) / 2;
+    p.groups = (p.nsub + 255) / 256;
+    p.group_size = (p.nsub + p.groups - 1) / p.groups;
+    h->fp_threads = ((p.group_size + 31) / 32) * 32;
+    const int nbox = (S + 7) / 8;
+    int tc = 32;
+    while (tc > 1 && (size_t)FP32_STAGES * nbox * tc * 128 > 100 * 1024) tc >>= 1;
+    p.tc = tc;
+    h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;
+}
+
+std::vector<int4> tc_items_for(int prob, int S, int units)
+{
+    std::vector<int4> v;
+    const int nb = tc_blocks(S);
+    v.reserve((size_t)units * nb * (nb + 1) / 2);
+    for (int u = 0; u < units; ++u)
+        for (int cb = 0; cb < nb; ++cb)
+            for (int rb = 0; rb <= cb; ++rb) v.push_back(make_int4(prob, u, rb, cb));
+    return v;
+}
+
+int bytes_per_sample(int dtype) { return dtype == CORR_CF32 ? 16 : dtype == CORR_CF16 ? 8 : 4; }
+
+TcProblem make_problem(const void *in, void *out, int S, int T, int units, int dtype)
+{
+    TcProblem pr{};
+    pr.in = in;
+    pr.out = out;
+    pr.S = S;
+    pr.T = T;
+    pr.n_units = units;
+    pr.in_unit_bytes = (long long)S * T * bytes_per_sample(dtype);
+    pr.out_unit_elems = n_baselines(S) * 4;
+    pr.vec = (((long long)T * bytes_per_sample(dtype)) % 16 == 0) ? 1 : 0;
+    return pr;
+}
+
+corr_status_t cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return CORR_OK;
+    if (e == cudaErrorMemoryAllocation) return CORR_ERR_NO_MEMORY;
+    return CORR_ERR_CUDA;
+}
+
+corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
+{
+    const corr_desc_t &d = h->d;
+    const long long units = (long long)d.n_channels * d.n_integrations;
+    const size_t out_bytes = (size_t)(units * n_baselines(d.n_stations) * 4 * 8);
+    if (d.n_samples == 0) return cuda_status(cudaMemsetAsync(d_out, 0, out_bytes, s));
+    if (h->path == CORR_PATH_FP32) {
+        CUtensorMap m;
+        corr_status_t st = encode_fp32_map(&m, d_in, d.n_stations, d.n_samples, (int)units, h->fp.tc);
+        if (st != CORR_OK) return st;
+        Fp32Params p = h->fp;
+        p.out = static_cast<float2 *>(d_out);
+        p.err = h->d_err;
+        p.wait_ns = h->wait_ns;
+        return cuda_status(fp32_launch(&m, p, h->fp_threads, h->fp_smem, s));
+    }
+    TcParams p{};
+    p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype);
+    p.probs = nullptr;
+    p.items = h->d_items;
+    p.n_items = h->n_items;
+    p.chunk_kb = d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
+    p.err = h->d_err;
+    p.wait_ns = h->wait_ns;
+    return cuda_status(tc_launch(d.dtype, p, h->tc_grid, s));
+}
+
+} // namespace
+
+extern "C" {
+
+const char *corr_status_string(corr_status_t s)
+{
+    switch (s) {
+    case CORR_OK: return "ok";
+    case CORR_ERR_INVALID_ARG: return "invalid argument";
+    case CORR_ERR_UNSUPPORTED: return "unsupported";
+    case CORR_ERR_NO_MEMORY: return "out of memory";
+    case CORR_ERR_CUDA: return "CUDA error";
+    case CORR_ERR_TIMEOUT: return "kernel gave up waiting (timeout)";
+    }
+    return "unknown status";
+}
+
+void corr_tile_cost(int w, int h, long *flops, long *bytes, long *regs)
+{
+    if (flops) *flops = 32L * w * h;
+    if (bytes) *bytes = 16L * (w + h);
+    if (regs) *regs = 4L * (1 + std::min(w, h)) + 8L * w * h;
+}
+
+int corr_tc_tiles(int S)
+{
+    if (S <= 0) return 0;
+    const int nb = tc_blocks(S);
+    return nb * (nb + 1) / 2;
+}
+
+int corr_tc_tile_decode(int S, int k, int *rb, int *cb)
+{
+    const int nb = tc_blocks(S);
+    if (S <= 0 || k < 0 || k >= nb * (nb + 1) / 2) return -1;
+    // order of tc_items_for: column block major, row block 0..cb
+    int c = 0;
+    while (k > c) {
+        k -= c + 1;
+        ++c;
+    }
+    if (rb) *rb = k;
+    if (cb) *cb = c;
+    return 0;
+}
+
+int corr_fp32_subtiles(int S)
+{
+    if (S <= 0) return 0;
+    const int nq = (S + 3) / 4;
+    return nq * (nq + 1) / 2;
+}
+
+int corr_fp32_subtile_decode(int S, int k, int *i, int *j)
+{
+    const int nq = (S + 3) / 4;
+    if (S <= 0 || k < 0 || k >= nq * (nq + 1) / 2) return -1;
+    int row = 0, off = 0;
+    while (k >= off + (nq - row)) {
+        off += nq - row;
+        ++row;
+    }
+    if (i) *i = row;
+    if (j) *j = row + (k - off);
+    return 0;
+}
+
+corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
+{
+    if (!out) return CORR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc) return CORR_ERR_INVALID_ARG;
+    const corr_desc_t &d = *desc;
+    if (d.n_stations < 1 || d.n_channels < 1 || d.n_samples < 0 || d.n_integrations < 1)
+        return CORR_ERR_INVALID_ARG;
+    if (d.n_pols != 2) return CORR_ERR_UNSUPPORTED;
+    if (d.dtype < CORR_CF32 || d.dtype > CORR_CI8) return CORR_ERR_INVALID_ARG;
+    if (d.path < CORR_PATH_AUTO || d.path > CORR_PATH_TENSOR) return CORR_ERR_INVALID_ARG;
+    int path = d.path;
+    if (path == CORR_PATH_AUTO) path = d.dtype == CORR_CF32 ? CORR_PATH_FP32 : CORR_PATH_TENSOR;
+    if (path == CORR_PATH_FP32 && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    if (path == CORR_PATH_TENSOR && d.dtype == CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    if (d.dtype == CORR_CI8 && d.n_samples > 65535) return CORR_ERR_UNSUPPORTED; // int32 range
+    const long long units = (long long)d.n_channels * d.n_integrations;
+    if (units > (1LL << 30) || d.n_stations > 65535) return CORR_ERR_UNSUPPORTED;
+    if ((d.flags & CORR_FLAG_GAINS) && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
+
+    corr_plan *h = new (std::nothrow) corr_plan();
+    if (!h) return CORR_ERR_NO_MEMORY;
+    h->d = d;
+    h->path = path;
+    if (const char *e = std::getenv("CORR_WAIT_LIMIT_NS")) h->wait_ns = std::strtoull(e, nullptr, 10);
+    corr_status_t st = CORR_OK;
+    do {
+        if ((st = cuda_status(cudaGetDevice(&h->device))) != CORR_OK) break;
+        if ((st = cuda_status(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount,
+                                                     h->device))) != CORR_OK)
+            break;
+        if ((st = cuda_status(cudaMalloc(&h->d_err, sizeof(int)))) != CORR_OK) break;
+        if ((st = cuda_status(cudaMemset(h->d_err, 0, sizeof(int)))) != CORR_OK) break;
+        if (path == CORR_PATH_FP32) {
+            fp32_config(h);
+        } else {
+            std::vector<int4> items = tc_items_for(0, d.n_stations, (int)units);
+            h->n_items = (int)items.size();
+            if ((st = cuda_status(cudaMalloc(&h->d_items, items.size() * sizeof(int4)))) != CORR_OK)
+                break;
+            if ((st = cuda_status(cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int4),
+                                             cudaMemcpyHostToDevice))) != CORR_OK)
+                break;
+            h->tc_grid = std::max(1, std::min(h->n_items, h->sm_count));
+        }
+        if (d.flags & CORR_FLAG_GAINS) {
+            const long long S = d.n_stations, N = 2 * S;
+            if ((st = cuda_status(cudaMalloc(&h->d_R, (size_t)(units * n_baselines(S) * 4 * 8)))) != CORR_OK) break;
+            if ((st = cuda_status(cudaMalloc(&h->d_W, (size_t)(units * N * N * 8)))) != CORR_OK) break;
+            if ((st = cuda_status(cudaMalloc(&h->d_partial, (size_t)units * sizeof(float)))) != CORR_OK) break;
+        }
+    } while (0);
+    if (st != CORR_OK) {
+        corr_destroy(h);
+        return st;
+    }
+    *out = h;
+    return CORR_OK;
+}
+
+corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream)
+{
+    if (!h || !d_in || !d_out) return CORR_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out)) return CORR_ERR_INVALID_ARG;
+    return launch_correlate(h, d_in, d_out, static_cast<cudaStream_t>(stream));
+}
+
+corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_subarray_t *subs,
+                                     void *stream)
+{
+    if (!h || n_sub < 0 || (n_sub > 0 && !subs)) return CORR_ERR_INVALID_ARG;
+    if (h->d.dtype == CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    if (n_sub == 0) return CORR_OK;
+    for (int i = 0; i < n_sub; ++i) {
+        const corr_subarray_t &s = subs[i];
+        if (s.n_stations < 1 || s.n_channels < 1 || s.n_samples < 0 || s.reserved != 0 || !s.d_in ||
+            !s.d_out || !aligned16(s.d_in) || !aligned16(s.d_out))
+            return CORR_ERR_INVALID_ARG;
+        if (h->d.dtype == CORR_CI8 && s.n_samples > 65535) return CORR_ERR_UNSUPPORTED;
+        if (s.n_stations > 65535) return CORR_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool same = (int)h->batch_key.size() == n_sub;
+    for (int i = 0; same && i < n_sub; ++i)
+        same = std::memcmp(&h->batch_key[i], &subs[i], sizeof(corr_subarray_t)) == 0;
+    if (!same) {
+        // Build the ragged work list: tiles of all sub-arrays, heaviest (longest
+        // integration) first so that the static round-robin split over the
+        // persistent CTAs ends evenly.
+        std::vector<TcProblem> probs;
+        std::vector<int4> items;
+        for (int i = 0; i < n_sub; ++i) {
+            const corr_subarray_t &s = subs[i];
+            probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
+                                         h->d.dtype));
+            if (s.n_samples == 0) continue;
+            std::vector<int4> v = tc_items_for(i, s.n_stations, s.n_channels);
+            items.insert(items.end(), v.begin(), v.end());
+        }
+        std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
+            return probs[a.x].T > probs[b.x].T;
+        });
+        cudaFree(h->d_bprobs);
+        cudaFree(h->d_bitems);
+        h->d_bprobs = nullptr;
+        h->d_bitems = nullptr;
+        h->batch_key.clear();
+        corr_status_t e;
+        if ((e = cuda_status(cudaMalloc(&h->d_bprobs, probs.size() * sizeof(TcProblem)))) != CORR_OK) return e;
+        if ((e = cuda_status(cudaMemcpy(h->d_bprobs, probs.data(), probs.size() * sizeof(TcProblem),
+                                        cudaMemcpyHostToDevice))) != CORR_OK)
+            return e;
+        if (!items.empty()) {
+            if ((e = cuda_status(cudaMalloc(&h->d_bitems, items.size() * sizeof(int4)))) != CORR_OK) return e;
+            if ((e = cuda_status(cudaMemcpy(h->d_bitems, items.data(), items.size() * sizeof(int4),
+                                            cudaMemcpyHostToDevice))) != CORR_OK)
+                return e;
+        }
+        h->n_bitems = (int)items.size();
+        h->batch_key.assign(subs, subs + n_sub);
+    }
+    for (int i = 0; i < n_sub; ++i)
+        if (subs[i].n_samples == 0) {
+            const size_t bytes = (size_t)subs[i].n_channels * n_baselines(subs[i].n_stations) * 4 * 8;
+            corr_status_t e = cuda_status(cudaMemsetAsync(subs[i].d_out, 0, bytes, st));
+            if (e != CORR_OK) return e;
+        }
+    if (h->n_bitems == 0) return CORR_OK;
+    TcParams p{};
+    p.probs = h->d_bprobs;
+    p.items = h->d_bitems;
+    p.n_items = h->n_bitems;
+    p.chunk_kb = h->d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
+    p.err = h->d_err;
+    p.wait_ns = h->wait_ns;
+    const int grid = std::max(1, std::min(h->n_bitems, h->sm_count));
+    return cuda_status(tc_launch(h->d.dtype, p, grid, st));
+}
+
+corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
+                             const void *d_vis_model, void *d_vis_out, float *d_loss, void *stream)
+{
+    if (!h || !d_raw_vis || !d_gain || !d_vis_model) return CORR_ERR_INVALID_ARG;
+    if (!(h->d.flags & CORR_FLAG_GAINS)) return CORR_ERR_INVALID_ARG;
+    const int units = h->d.n_channels * h->d.n_integrations;
+    return cuda_status(gain_loss_launch(static_cast<const float2 *>(d_raw_vis),
+                                        static_cast<const float2 *>(d_gain),
+                                        static_cast<const float2 *>(d_vis_model),
+                                        static_cast<float2 *>(d_vis_out), h->d_partial, d_loss,
+                                        h->d.n_stations, units, static_cast<cudaStream_t>(stream)));
+}
+
+corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *d_gain,
+                                 const void *d_vis_model, const void *d_raw_vis, void *d_grad_gain,
+                                 void *d_grad_in, float *d_loss, const float *d_grad_scale,
+                                 void *stream)
+{
+    if (!h || !d_gain || !d_vis_model || !d_grad_gain) return CORR_ERR_INVALID_ARG;
+    if (!(h->d.flags & CORR_FLAG_GAINS)) return CORR_ERR_INVALID_ARG;
+    if ((!d_raw_vis || d_grad_in) && !d_in) return CORR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int units = h->d.n_channels * h->d.n_integrations;
+    const int S = h->d.n_stations;
+    const float2 *R = static_cast<const float2 *>(d_raw_vis);
+    if (!R) {
+        corr_status_t e = corr_correlate(h, d_in, h->d_R, stream);
+        if (e != CORR_OK) return e;
+        R = h->d_R;
+    }
+    const float2 *g = static_cast<const float2 *>(d_gain);
+    const float2 *M = static_cast<const float2 *>(d_vis_model);
+    corr_status_t e = cuda_status(gain_grad_launch(R, g, M, d_grad_scale,
+                                                   static_cast<float2 *>(d_grad_gain), S, units, st));
+    if (e != CORR_OK) return e;
+    if (d_grad_in) {
+        e = cuda_status(input_grad_launch(static_cast<const float2 *>(d_in), R, g, M, d_grad_scale,
+                                          h->d_W, static_cast<float2 *>(d_grad_in), S,
+                                          h->d.n_samples, units, st));
+        if (e != CORR_OK) return e;
+    }
+    if (d_loss)
+        e = cuda_status(gain_loss_launch(R, g, M, nullptr, h->d_partial, d_loss, S, units, st));
+    return e;
+}
+
+corr_status_t corr_get_error(corr_handle_t h)
+{
+    if (!h) return CORR_ERR_INVALID_ARG;
+    int v = 0;
+    corr_status_t e = cuda_status(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != CORR_OK) return e;
+    if (v) {
+        e = cuda_status(cudaMemset(h->d_err, 0, sizeof(int)));
+        if (e != CORR_OK) return e;
+        return CORR_ERR_TIMEOUT;
+    }
+    return CORR_OK;
+}
+
+corr_status_t corr_destroy(corr_handle_t h)
+{
+    if (!h) return CORR_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_err);
+    cudaFree(h->d_items);
+    cudaFree(h->d_bprobs);
+    cudaFree(h->d_bitems);
+    cudaFree(h->d_R);
+    cudaFree(h->d_W);
+    cudaFree(h->d_partial);
+    delete h;
+    return CORR_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,168 @@
+// FP32 CUDA-core correlator.
+//
+// Section 2's register tiling of the correlation triangle: each thread owns
+// a 4x4-station tile (16 baselines x 4 polarisation pairs = 128 FP32
+// accumulators kept in registers for the whole integration) and performs
+// the conjugate multiply-add with four FMAs,
+//     acc_r += a_r b_r + a_i b_i,   acc_i += a_i b_r - a_r b_i,
+// reusing each loaded sample against 4 partner stations (Table 1, 4x4 tile:
+// 512 flops per 128 bytes loaded). Tiles in the same row of the triangle are
+// assigned to neighbouring threads so they consume the same samples at the
+// same time (Section 2's inter-tile reuse through co-scheduling).
+//
+// Samples are staged by TMA: each stage holds `tc` samples of every station
+// the CTA needs, as boxes of 8 stations stored time-major
+// ([box][t][8 stations][2 pols x complex]). Thread j reads its four column
+// stations in the rotated order 4j + ((k + j/2) mod 4) so that the 8
+// threads of a quarter-warp read 8 distinct 16-byte bank groups; the rotation
+// is undone when the result is stored.
+#include <cuda.h>
+#include "corr_internal.h"
+#include "ptx.cuh"
+
+namespace corr {
+
+namespace {
+
+__device__ __forceinline__ void decode_subtile(int nq, int k, int &i, int &j)
+{
+    // row-major upper triangle: row i holds columns i..nq-1
+    int row = 0, off = 0;
+    while (k >= off + (nq - row)) {
+        off += nq - row;
+        ++row;
+    }
+    i = row;
+    j = row + (k - off);
+}
+
+__global__ void __launch_bounds__(256) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const Fp32Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ uint64_t full[FP32_STAGES];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int unit = blockIdx.x / p.groups;
+    const int grp = blockIdx.x % p.groups;
+    const int k_first = grp * p.group_size;
+    const int k = k_first + tid;
+    const bool active = tid < p.group_size && k < p.nsub;
+
+    int i, j, i_first, j_first;
+    decode_subtile(p.nq, active ? k : k_first, i, j);
+    decode_subtile(p.nq, k_first, i_first, j_first);
+    const int s_lo = (4 * i_first) & ~7;
+    const int nbox = (p.S - s_lo + 7) / 8;
+    const int box_f4 = p.tc * 8;                 // float4 per box
+    const int stage_f4 = nbox * box_f4;
+    const uint32_t stage_bytes = (uint32_t)stage_f4 * 16u;
+    const int nchunks = (p.T + p.tc - 1) / p.tc;
+
+    if (tid == 0) {
+        prefetch_tmap(&tmap);
+        for (int s = 0; s < FP32_STAGES; ++s) mbar_init(&full[s], 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int kc) {
+        const int st = kc % FP32_STAGES;
+        mbar_arrive_expect_tx(&full[st], stage_bytes);
+        for (int b = 0; b < nbox; ++b)
+            tma_load_4d(smem + (size_t)st * stage_bytes + (size_t)b * box_f4 * 16, &tmap, &full[st],
+                        0, s_lo + 8 * b, kc * p.tc, unit);
+    };
+    if (tid == 0)
+        for (int kc = 0; kc < FP32_STAGES && kc < nchunks; ++kc) issue(kc);
+
+    int row_off[4], col_off[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = 4 * i + a - s_lo;
+        row_off[a] = (r >> 3) * box_f4 + (r & 7);
+        const int c = 4 * j + ((a + (j >> 1)) & 3) - s_lo;
+        col_off[a] = (c >> 3) * box_f4 + (c & 7);
+    }
+
+    float acc[4][4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[a][b][q] = 0.f;
+
+    const float4 *sm4 = reinterpret_cast<const float4 *>(smem);
+    for (int kc = 0; kc < nchunks; ++kc) {
+        const int st = kc % FP32_STAGES;
+        const bool ok = mbar_wait_bounded(&full[st], (kc / FP32_STAGES) & 1, &abort_flag, p.err,
+                                          p.wait_ns);
+        if (ok) {
+            const float4 *base = sm4 + (size_t)st * stage_f4;
+            const int tn = min(p.tc, p.T - kc * p.tc);
+#pragma unroll 2
+            for (int t = 0; t < tn; ++t) {
+                float4 r[4], c[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) r[a] = base[row_off[a] + t * 8];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) c[b] = base[col_off[b] + t * 8];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        float *q = acc[a][b];
+                        // (p1, p2) = (0,0), (0,1), (1,0), (1,1); entries (re, im)
+                        q[0] = fmaf(r[a].x, c[b].x, q[0]); q[0] = fmaf(r[a].y, c[b].y, q[0]);
+                        q[1] = fmaf(r[a].y, c[b].x, q[1]); q[1] = fmaf(-r[a].x, c[b].y, q[1]);
+                        q[2] = fmaf(r[a].x, c[b].z, q[2]); q[2] = fmaf(r[a].y, c[b].w, q[2]);
+                        q[3] = fmaf(r[a].y, c[b].z, q[3]); q[3] = fmaf(-r[a].x, c[b].w, q[3]);
+                        q[4] = fmaf(r[a].z, c[b].x, q[4]); q[4] = fmaf(r[a].w, c[b].y, q[4]);
+                        q[5] = fmaf(r[a].w, c[b].x, q[5]); q[5] = fmaf(-r[a].z, c[b].y, q[5]);
+                        q[6] = fmaf(r[a].z, c[b].z, q[6]); q[6] = fmaf(r[a].w, c[b].w, q[6]);
+                        q[7] = fmaf(r[a].w, c[b].z, q[7]); q[7] = fmaf(-r[a].z, c[b].w, q[7]);
+                    }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0 && kc + FP32_STAGES < nchunks) issue(kc + FP32_STAGES);
+    }
+
+    if (!active || abort_flag) return;
+    const long long B = (long long)p.S * (p.S + 1) / 2;
+    float2 *out = p.out + (long long)unit * B * 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int s1 = 4 * i + a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int s2 = 4 * j + ((b + (j >> 1)) & 3);
+            if (s1 <= s2 && s2 < p.S) {
+                float4 *dst = reinterpret_cast<float4 *>(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4);
+                dst[0] = make_float4(acc[a][b][0], acc[a][b][1], acc[a][b][2], acc[a][b][3]);
+                dst[1] = make_float4(acc[a][b][4], acc[a][b][5], acc[a][b][6], acc[a][b][7]);
+            }
+        }
+    }
+}
+
+} // namespace
+
+cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int threads, size_t smem,
+                        cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+    fp32_correlate_kernel<<<p.n_units * p.groups, threads, smem, s>>>(*m, p);
+    return cudaGetLastError();
+}
+
+} // namespace corr

@@ -1,0 +1,250 @@
+// Gain-calibration loss and its hand-written adjoint (FP32).
+//
+// The correlator output feeds calibration (Section 2 keeps autocorrelations
+// for it). With per-station, per-polarisation complex gains g and samples x,
+// y = g x, the visibilities of y are V_ab = g_a conj(g_b) R_ab with R the
+// correlation of x. For a model M the loss is L = sum |V_ab - M_ab|^2 over
+// baselines s1 <= s2 and all polarisation pairs. Gradients follow PyTorch's
+// convention for a real function of complex inputs, grad = 2 dL/d conj(z):
+//   dL/d conj(g_c)   = sum_{(c,b)} E_cb g_b conj(R_cb) + sum_{(a,c)} conj(E_ac) g_a R_ac
+//   dL/d conj(x_c(t)) = conj(g_c) sum_b W_cb g_b x_b(t),
+//   W_cb = [s_c <= s_b] E_cb + [s_b <= s_c] conj(E_bc),   E = V - M.
+// The input gradient is a complex GEMM per channel: W' = 2 conj(g) W g is
+// formed once, then grad_x[c][t] = sum_b W'[c][b] x[b][t].
+#include "corr_internal.h"
+
+namespace corr {
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ long long bl(int s1, int s2) { return (long long)s2 * (s2 + 1) / 2 + s1; }
+
+// E_ab for a = (s1,p1), b = (s2,p2), s1 <= s2.
+__device__ __forceinline__ float2 residual(const float2 *R, const float2 *g, const float2 *M,
+                                           int s1, int p1, int s2, int p2)
+{
+    const long long k = bl(s1, s2) * 4 + p1 * 2 + p2;
+    const float2 w = cmul(g[s1 * 2 + p1], cconj(g[s2 * 2 + p2]));
+    const float2 v = cmul(w, R[k]);
+    return make_float2(v.x - M[k].x, v.y - M[k].y);
+}
+
+__global__ void gain_loss_kernel(const float2 *R, const float2 *g, const float2 *M, float2 *V,
+                                 float *partial, int S)
+{
+    const int unit = blockIdx.x;
+    const long long B4 = (long long)S * (S + 1) / 2 * 4;
+    const float2 *Ru = R + unit * B4;
+    const float2 *Mu = M + unit * B4;
+    const float2 *gu = g + (long long)unit * S * 2;
+    float sum = 0.f;
+    for (long long k = threadIdx.x; k < B4; k += blockDim.x) {
+        const long long b = k >> 2;
+        const int p1 = (k >> 1) & 1, p2 = k & 1;
+        // invert b = s2(s2+1)/2 + s1
+        int s2 = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        while ((long long)s2 * (s2 + 1) / 2 > b) --s2;
+        while ((long long)(s2 + 1) * (s2 + 2) / 2 <= b) ++s2;
+        const int s1 = (int)(b - (long long)s2 * (s2 + 1) / 2);
+        const float2 w = cmul(gu[s1 * 2 + p1], cconj(gu[s2 * 2 + p2]));
+        const float2 v = cmul(w, Ru[k]);
+        if (V) V[unit * B4 + k] = v;
+        const float er = v.x - Mu[k].x, ei = v.y - Mu[k].y;
+        sum = fmaf(er, er, fmaf(ei, ei, sum));
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[unit] = red[0];
+}
+
+__global__ void sum_partials_kernel(const float *partial, int n, float *loss)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0];
+}
+
+// One thread per (unit, c = (s, p)): both sums of dL/d conj(g_c).
+__global__ void gain_grad_kernel(const float2 *R, const float2 *g, const float2 *M,
+                                 const float *scale, float2 *grad, int S, int units)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = 2 * S;
+    if (idx >= (long long)units * N) return;
+    const int unit = (int)(idx / N);
+    const int c = (int)(idx % N);
+    const int sc = c >> 1, pc = c & 1;
+    const long long B4 = (long long)S * (S + 1) / 2 * 4;
+    const float2 *Ru = R + unit * B4;
+    const float2 *Mu = M + unit * B4;
+    const float2 *gu = g + (long long)unit * N;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < N; ++b) {
+        const int sb = b >> 1, pb = b & 1;
+        if (sc <= sb) { // (c, b) in the triangle: E_cb g_b conj(R_cb)
+            const float2 e = residual(Ru, gu, Mu, sc, pc, sb, pb);
+            const float2 r = Ru[bl(sc, sb) * 4 + pc * 2 + pb];
+            const float2 t = cmul(cmul(e, gu[b]), cconj(r));
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+        if (sb <= sc) { // (b, c) in the triangle: conj(E_bc) g_b R_bc
+            const float2 e = residual(Ru, gu, Mu, sb, pb, sc, pc);
+            const float2 r = Ru[bl(sb, sc) * 4 + pb * 2 + pc];
+            const float2 t = cmul(cmul(cconj(e), gu[b]), r);
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+    }
+    const float s = 2.f * (scale ? *scale : 1.f);
+    grad[idx] = make_float2(s * acc.x, s * acc.y);
+}
+
+// W'[unit][c][b] = 2 scale conj(g_c) W_cb g_b.
+__global__ void build_w_kernel(const float2 *R, const float2 *g, const float2 *M,
+                               const float *scale, float2 *W, int S, int units)
+{
+    const int N = 2 * S;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)units * N * N) return;
+    const int unit = (int)(idx / ((long long)N * N));
+    const int c = (int)((idx / N) % N);
+    const int b = (int)(idx % N);
+    const int sc = c >> 1, pc = c & 1, sb = b >> 1, pb = b & 1;
+    const long long B4 = (long long)S * (S + 1) / 2 * 4;
+    const float2 *Ru = R + unit * B4;
+    const float2 *Mu = M + unit * B4;
+    const float2 *gu = g + (long long)unit * N;
+    float2 w = make_float2(0.f, 0.f);
+    if (sc <= sb) {
+        const float2 e = residual(Ru, gu, Mu, sc, pc, sb, pb);
+        w.x += e.x;
+        w.y += e.y;
+    }
+    if (sb <= sc) {
+        const float2 e = residual(Ru, gu, Mu, sb, pb, sc, pc);
+        w.x += e.x;
+        w.y -= e.y;
+    }
+    const float s = 2.f * (scale ? *scale : 1.f);
+    const float2 v = cmul(cmul(cconj(gu[c]), w), gu[b]);
+    W[idx] = make_float2(s * v.x, s * v.y);
+}
+
+// grad_x[unit][s][t][p] = sum_b W'[unit][(s,p)][b] x[unit][b][t], b = (s', p').
+// CTA tile: 64 rows (c) x 64 times; thread tile 4 rows x 4 times.
+__global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, const float2 *x,
+                                                              float2 *gx, int S, int T)
+{
+    const int N = 2 * S;
+    const int unit = blockIdx.z;
+    const int c0 = blockIdx.y * 64;
+    const int t0 = blockIdx.x * 64;
+    const float2 *Wu = W + (long long)unit * N * N;
+    const float2 *xu = x + (long long)unit * S * T * 2;
+    float2 *gu = gx + (long long)unit * S * T * 2;
+    __shared__ float2 Ws[64][17];
+    __shared__ float2 Xs[16][64];
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+
+    for (int b0 = 0; b0 < N; b0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int r = e >> 4, k = e & 15;
+            const int c = c0 + r, b = b0 + k;
+            Ws[r][k] = (c < N && b < N) ? Wu[(long long)c * N + b] : make_float2(0.f, 0.f);
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            // e -> (station-local, t, pol) in memory order of x
+            const int sl = e >> 7, rem = e & 127, tt = rem >> 1, pp = rem & 1;
+            const int s = (b0 >> 1) + sl, t = t0 + tt;
+            Xs[2 * sl + pp][tt] = (s < S && t < T) ? xu[((long long)s * T + t) * 2 + pp]
+                                                   : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float2 wv[4], xv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) wv[a] = Ws[ty * 4 + a][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] = Xs[k][tx * 4 + q];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[a][q].x = fmaf(wv[a].x, xv[q].x, fmaf(-wv[a].y, xv[q].y, acc[a][q].x));
+                    acc[a][q].y = fmaf(wv[a].x, xv[q].y, fmaf(wv[a].y, xv[q].x, acc[a][q].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int c = c0 + ty * 4 + a;
+        if (c >= N) continue;
+        const int s = c >> 1, pp = c & 1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = t0 + tx * 4 + q;
+            if (t < T) gu[((long long)s * T + t) * 2 + pp] = acc[a][q];
+        }
+    }
+}
+
+} // namespace
+
+cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, float2 *V,
+                             float *partial, float *loss, int S, int units, cudaStream_t s)
+{
+    gain_loss_kernel<<<units, 256, 0, s>>>(R, g, M, V, partial, S);
+    if (loss) sum_partials_kernel<<<1, 256, 0, s>>>(partial, units, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
+                             const float *scale, float2 *grad_g, int S, int units,
+                             cudaStream_t s)
+{
+    const long long n = (long long)units * 2 * S;
+    gain_grad_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(R, g, M, scale, grad_g, S, units);
+    return cudaGetLastError();
+}
+
+cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
+                              const float2 *M, const float *scale, float2 *W,
+                              float2 *grad_x, int S, int T, int units, cudaStream_t s)
+{
+    const long long N = 2LL * S;
+    const long long n = (long long)units * N * N;
+    build_w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, g, M, scale, W, S, units);
+    if (T > 0) {
+        dim3 grid((T + 63) / 64, (unsigned)((N + 63) / 64), units);
+        input_grad_gemm_kernel<<<grid, 256, 0, s>>>(W, x, grad_x, S, T);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace corr

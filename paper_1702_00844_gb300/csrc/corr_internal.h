@@ -1,0 +1,63 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace corr {
+
+// ---------------------------------------------------------------- tensor path
+// One correlation problem for the tcgen05 kernel: n_units independent
+// channels (integrations x channels) of S stations and T samples.
+struct TcProblem {
+    const void *in;           // [unit][S][T][2 pols] complex f16 or int8
+    void *out;                // [unit][S(S+1)/2][2][2] complex f32 or int32
+    long long in_unit_bytes;  // S*T*2*sizeof(complex sample)
+    long long out_unit_elems; // S(S+1)/2 * 4 complex values
+    int S, T, n_units, vec;   // vec: 16-byte vector loads are aligned
+};
+
+struct TcParams {
+    TcProblem prob0;          // used when probs == nullptr
+    const TcProblem *probs;   // device array (ragged batches)
+    const int4 *items;        // {problem, unit, row block, col block}
+    int n_items;
+    int chunk_kb;             // K-blocks per exact accumulation chunk (0 = all)
+    int *err;                 // device error word
+    unsigned long long wait_ns;
+};
+
+enum TcVariant { TC_N128 = 0 };
+
+constexpr int TC_RS = 64;      // stations per tile side
+constexpr int TC_KB_T = 32;    // time samples per K-block
+constexpr int TC_STAGES = 6;
+constexpr int TC_THREADS = 13 * 32;
+constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
+
+size_t tc_smem_bytes();
+cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s);
+
+// ------------------------------------------------------------------ FP32 path
+struct Fp32Params {
+    float2 *out;
+    int S, T, n_units;
+    int nq, nsub, groups, group_size; // 4x4 sub-tiles per unit and grouping
+    int tc;                           // samples per pipeline stage
+    int *err;
+    unsigned long long wait_ns;
+};
+constexpr int FP32_STAGES = 3;
+cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int threads, size_t smem,
+                        cudaStream_t s);
+
+// -------------------------------------------------------------- gain adjoint
+cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, float2 *V,
+                             float *partial, float *loss, int S, int units, cudaStream_t s);
+cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
+                             const float *scale, float2 *grad_g, int S, int units,
+                             cudaStream_t s);
+cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
+                              const float2 *M, const float *scale, float2 *W,
+                              float2 *grad_x, int S, int T, int units, cudaStream_t s);
+
+} // namespace corr

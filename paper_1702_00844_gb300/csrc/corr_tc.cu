@@ -1,0 +1,441 @@
+// Tensor-core correlator (tcgen05, kind::f16, FP32 accumulation in TMEM).
+//
+// Per channel the X-step of Section 2 is the Hermitian product V = X X^H of
+// the (station, pol) x time sample matrix. With a = x_{s1,p1}(t) and
+// b = x_{s2,p2}(t),
+//     Re V_ab = sum_t (a_r b_r + a_i b_i),   Im V_ab = sum_t (a_i b_r - a_r b_i),
+// i.e. the four FMAs of Section 2 expressed as real matrix products. Each
+// operand row (station, pol) holds, per block of 32 samples, the 32 real
+// parts followed by the 32 imaginary parts (64 f16 = one 128-byte swizzle
+// row). With K-steps k0,k1 = real parts and k2,k3 = imaginary parts:
+//     Re += A[k0]B[k0] + A[k1]B[k1] + A[k2]B[k2] + A[k3]B[k3]
+//     Im += A[k2]B[k0] + A[k3]B[k1] - A[k0]B[k2] - A[k1]B[k3]   (negate-A bit)
+// so no rotated copy of either operand is needed.
+//
+// Work is a triangular schedule of 64x64-station tiles (row block <= column
+// block, Section 2's tiling of the correlation triangle; blocks of stations as
+// for large station counts in Section 5): a persistent CTA per SM walks its
+// share of the (problem, channel, tile) list.
+//
+// Warp roles (416 threads):
+//   warps 0-7  : load samples (coalesced 16-byte loads), widen int8 to f16
+//                exactly, split polarisations and real/imaginary parts, and
+//                store both operand tiles in the 128-byte swizzled K-major
+//                layout of a ring of shared-memory stages;
+//   warps 8-11 : epilogue: TMEM -> registers, mask s1 <= s2, store
+//                [channel][baseline][p1][p2] once (int8: fold each 512-sample
+//                chunk into INT32 exactly);
+//   warp 12    : allocates TMEM (2 accumulator buffers x (Re 128 + Im 128)
+//                columns) and issues the MMAs (one thread).
+// Every wait is bounded (see mbar_wait_bounded).
+#include "corr_internal.h"
+#include "ptx.cuh"
+
+namespace corr {
+
+namespace {
+
+constexpr int TILE_BYTES = 128 * 128;        // 128 rows x 128 B
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B operand tiles
+constexpr int N_PRODUCERS = 256;
+constexpr int N_EPILOGUE = 128;
+constexpr int WARP_MMA = 12;
+constexpr uint32_t TMEM_COLS = 512;
+
+struct Bars {
+    uint64_t full[TC_STAGES];
+    uint64_t empty[TC_STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t fin;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+template <int DT> struct Raw;          // raw samples of 8 times of one station
+template <> struct Raw<1> { uint4 v[4]; }; // complex f16 x 2 pols: 64 bytes
+template <> struct Raw<2> { uint4 v[2]; }; // complex int8 x 2 pols: 32 bytes
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Loads samples t0..t0+7 of station s (zeros outside [0,S) x [0,T)).
+template <int DT>
+__device__ __forceinline__ void load_raw(const uint8_t *unit_in, int S, int T, bool vec, int s,
+                                         int t0, Raw<DT> &r)
+{
+    constexpr int BPT = DT == 1 ? 8 : 4; // bytes per time sample (2 pols, re+im)
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q) r.v[q] = make_uint4(0, 0, 0, 0);
+    if (s >= S || t0 >= T) return;
+    const uint8_t *p = unit_in + ((size_t)s * T + t0) * BPT;
+    if (vec && t0 + 8 <= T) {
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q)
+            r.v[q] = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+        return;
+    }
+    uint32_t w[sizeof(Raw<DT>) / 4];
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(Raw<DT>) / 4); ++i) w[i] = 0;
+#pragma unroll
+    for (int tt = 0; tt < 8; ++tt) {
+        if (t0 + tt < T) {
+            if (DT == 1) {
+                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p + tt * 8));
+                w[2 * tt] = u.x;
+                w[2 * tt + 1] = u.y;
+            } else {
+                w[tt] = __ldg(reinterpret_cast<const uint32_t *>(p + tt * 4));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q)
+        r.v[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+// Two int8 (as the low bytes of the two halves of u) -> two exact f16:
+// half bits 0x6400 | (v ^ 0x80) encode 1024 + (v + 128); subtracting 1152
+// leaves v exactly (all integers of magnitude <= 2048 are f16 values).
+__device__ __forceinline__ uint32_t i8pair_to_h2(uint32_t u)
+{
+    uint32_t b = (u & 0x00FF00FFu) ^ 0x64806480u;
+    __half2 h = *reinterpret_cast<__half2 *>(&b);
+    const __half2 off = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));
+    __half2 d = __hsub2(h, off);
+    return *reinterpret_cast<uint32_t *>(&d);
+}
+
+// Splits 8 samples of one station into 4 chunks of 8 f16 each:
+// re[p] = real parts of pol p, im[p] = imaginary parts of pol p.
+template <int DT>
+__device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&im)[2])
+{
+    uint32_t o_re[2][4], o_im[2][4];
+    if (DT == 1) {
+        // word 2t+p = (re, im) of pol p at time t (low half = re)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i0 = 2 * (2 * q) + p, i1 = 2 * (2 * q + 1) + p;
+                const uint32_t w0 = word_of(r.v[i0 >> 2], i0 & 3);
+                const uint32_t w1 = word_of(r.v[i1 >> 2], i1 & 3);
+                o_re[p][q] = __byte_perm(w0, w1, 0x5410);
+                o_im[p][q] = __byte_perm(w0, w1, 0x7632);
+            }
+    } else {
+        // word t = bytes (p0 re, p0 im, p1 re, p1 im) at time t
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t w0 = word_of(r.v[(2 * q) >> 2], (2 * q) & 3);
+                const uint32_t w1 = word_of(r.v[(2 * q + 1) >> 2], (2 * q + 1) & 3);
+                const uint32_t sre = (uint32_t)(2 * p) | ((uint32_t)(4 + 2 * p) << 8);
+                const uint32_t sim = (uint32_t)(2 * p + 1) | ((uint32_t)(5 + 2 * p) << 8);
+                o_re[p][q] = i8pair_to_h2(__byte_perm(w0, w1, sre));
+                o_im[p][q] = i8pair_to_h2(__byte_perm(w0, w1, sim));
+            }
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        re[p] = make_uint4(o_re[p][0], o_re[p][1], o_re[p][2], o_re[p][3]);
+        im[p] = make_uint4(o_im[p][0], o_im[p][1], o_im[p][2], o_im[p][3]);
+    }
+}
+
+// Stores the 4 chunks of station-local sl, time group g into a 128-row tile
+// (row = 2*sl + pol; chunk g = real parts, chunk 4+g = imaginary parts) in the
+// 128-byte swizzled layout. The order of the four stores alternates with the
+// station parity so that each quarter-warp hits 8 distinct 16-byte bank groups.
+template <int DT>
+__device__ __forceinline__ void store_tile(uint8_t *tile, int sl, int g, const Raw<DT> &r)
+{
+    uint4 re[2], im[2];
+    split<DT>(r, re, im);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int p = k >> 1;
+        const int part = (k ^ sl) & 1;
+        const int row = 2 * sl + p;
+        const int chunk = g + 4 * part;
+        uint4 v = part ? im[p] : re[p];
+        *reinterpret_cast<uint4 *>(tile + row * 128 + ((chunk ^ (row & 7)) << 4)) = v;
+    }
+}
+
+struct Item {
+    int prob, unit, rb, cb;
+};
+
+__device__ __forceinline__ Item get_item(const TcParams &p, int i)
+{
+    const int4 v = __ldg(p.items + i);
+    return Item{v.x, v.y, v.z, v.w};
+}
+
+__device__ __forceinline__ TcProblem get_prob(const TcParams &p, int k)
+{
+    return p.probs ? p.probs[k] : p.prob0;
+}
+
+__device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
+{
+    return chunk_kb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *tiles = smem;
+    Bars *bars = reinterpret_cast<Bars *>(smem + TC_STAGES * STAGE_BYTES);
+    volatile int *abort_flag = &bars->abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&bars->full[s], N_PRODUCERS);
+            mbar_init(&bars->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], N_EPILOGUE);
+        }
+        mbar_init(&bars->fin, 1);
+        bars->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == WARP_MMA) {
+        tmem_alloc(&bars->tmem_base, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = bars->tmem_base;
+
+    if (warp < 8) {
+        // ------------------------------------------------------ producers
+        const int pt = tid;          // 0..255
+        const int sl = pt >> 2;      // station within the tile
+        const int g = pt & 3;        // group of 8 samples within the K-block
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+            const Item item = get_item(p, it);
+            const TcProblem P = get_prob(p, item.prob);
+            const bool diag = item.rb == item.cb;
+            const uint8_t *unit_in = static_cast<const uint8_t *>(P.in) +
+                                     (size_t)item.unit * (size_t)P.in_unit_bytes;
+            const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
+            const int sa = item.rb * TC_RS + sl;
+            const int sb = item.cb * TC_RS + sl;
+            const bool vec = P.vec != 0;
+            Raw<DT> ra[2], rbv[2];
+            load_raw<DT>(unit_in, P.S, P.T, vec, sa, 8 * g, ra[0]);
+            if (!diag) load_raw<DT>(unit_in, P.S, P.T, vec, sb, 8 * g, rbv[0]);
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; kb += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kb + h;
+                    if (k < nkb) {
+                        if (k + 1 < nkb) {
+                            load_raw<DT>(unit_in, P.S, P.T, vec, sa, (k + 1) * TC_KB_T + 8 * g,
+                                         ra[h ^ 1]);
+                            if (!diag)
+                                load_raw<DT>(unit_in, P.S, P.T, vec, sb,
+                                             (k + 1) * TC_KB_T + 8 * g, rbv[h ^ 1]);
+                        }
+                        if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
+                                               p.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *st = tiles + stage * STAGE_BYTES;
+                        store_tile<DT>(st, sl, g, ra[h]);
+                        if (!diag) store_tile<DT>(st + TILE_BYTES, sl, g, rbv[h]);
+                        fence_proxy_async_smem();
+                        mbar_arrive(&bars->full[stage]);
+                        if (++stage == TC_STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                }
+            }
+            if (!ok) break;
+        }
+    } else if (warp < 12) {
+        // ------------------------------------------------------- epilogue
+        const int eq = warp - 8;            // TMEM lane quarter of this warp
+        const int row = eq * 32 + lane;     // A row = 2*station + pol
+        const int sl = row >> 1;
+        const int p1 = row & 1;
+        uint32_t acc_it = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+            const Item item = get_item(p, it);
+            const TcProblem P = get_prob(p, item.prob);
+            const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
+            const int nch = n_chunks(nkb, p.chunk_kb);
+            const int s1 = item.rb * TC_RS + sl;
+            for (int c = 0; c < nch; ++c, ++acc_it) {
+                const uint32_t buf = acc_it & 1, ap = (acc_it >> 1) & 1;
+                if (!mbar_wait_bounded(&bars->acc_full[buf], ap, abort_flag, p.err, p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + buf * 256 + ((uint32_t)(eq * 32) << 16);
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    uint32_t vre[32], vim[32];
+                    tmem_ld_32x32b_x32(taddr + cc * 32, vre);
+                    tmem_ld_32x32b_x32(taddr + 128 + cc * 32, vim);
+                    tmem_wait_ld();
+                    const int s2_0 = item.cb * TC_RS + cc * 16;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int s2 = s2_0 + j;
+                        if (s1 <= s2 && s2 < P.S) {
+                            const long long idx =
+                                (long long)item.unit * P.out_unit_elems +
+                                ((long long)s2 * (s2 + 1) / 2 + s1) * 4 + p1 * 2;
+                            if (DT == 1) {
+                                float4 v = make_float4(
+                                    __uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
+                                    __uint_as_float(vre[2 * j + 1]),
+                                    __uint_as_float(vim[2 * j + 1]));
+                                *reinterpret_cast<float4 *>(static_cast<float2 *>(P.out) + idx) = v;
+                            } else {
+                                int4 v = make_int4(__float2int_rn(__uint_as_float(vre[2 * j])),
+                                                   __float2int_rn(__uint_as_float(vim[2 * j])),
+                                                   __float2int_rn(__uint_as_float(vre[2 * j + 1])),
+                                                   __float2int_rn(__uint_as_float(vim[2 * j + 1])));
+                                int4 *dst = reinterpret_cast<int4 *>(static_cast<int2 *>(P.out) + idx);
+                                if (c > 0) {
+                                    const int4 o = *dst;
+                                    v.x += o.x;
+                                    v.y += o.y;
+                                    v.z += o.z;
+                                    v.w += o.w;
+                                }
+                                *dst = v;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bars->acc_empty[buf]);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ MMA
+        constexpr uint32_t IDESC = idesc_f16_f32(128, 128, false);
+        constexpr uint32_t IDESC_NEG = idesc_f16_f32(128, 128, true);
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t acc_it = 0;
+        bool ok = true;
+        const uint32_t tiles_u32 = smem_u32(tiles);
+        for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+            const Item item = get_item(p, it);
+            const TcProblem P = get_prob(p, item.prob);
+            const bool diag = item.rb == item.cb;
+            const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
+            const int nch = n_chunks(nkb, p.chunk_kb);
+            const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
+            for (int c = 0; c < nch && ok; ++c, ++acc_it) {
+                const uint32_t buf = acc_it & 1, ap = (acc_it >> 1) & 1;
+                if (!mbar_wait_bounded(&bars->acc_empty[buf], ap ^ 1, abort_flag, p.err,
+                                       p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_re = tmem_base + buf * 256;
+                const uint32_t d_im = d_re + 128;
+                const int kb_lo = c * ckb;
+                const int kb_hi = min(nkb, kb_lo + ckb);
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                    if (!mbar_wait_bounded(&bars->full[stage], phase, abort_flag, p.err,
+                                           p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (lane == 0) {
+                        const uint32_t a = tiles_u32 + stage * STAGE_BYTES;
+                        const uint32_t b = diag ? a : a + TILE_BYTES;
+                        const uint32_t first = kb == kb_lo ? 1u : 0u;
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks)
+                            tc_mma_f16(d_re, smem_desc_sw128(a + 32 * ks),
+                                       smem_desc_sw128(b + 32 * ks), IDESC,
+                                       (first && ks == 0) ? 0u : 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 64), smem_desc_sw128(b + 0), IDESC,
+                                   first ? 0u : 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 96), smem_desc_sw128(b + 32), IDESC, 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 0), smem_desc_sw128(b + 64), IDESC_NEG, 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 32), smem_desc_sw128(b + 96), IDESC_NEG, 1u);
+                        tc_commit(&bars->empty[stage]);
+                    }
+                    __syncwarp();
+                    if (++stage == TC_STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                if (lane == 0) tc_commit(&bars->acc_full[buf]);
+                __syncwarp();
+            }
+        }
+        // Wait (bounded) for every MMA this thread issued before TMEM is freed.
+        if (lane == 0) tc_commit(&bars->fin);
+        __syncwarp();
+        int dummy_abort = 0;
+        mbar_wait_bounded(&bars->fin, 0, &dummy_abort, p.err, p.wait_ns);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == WARP_MMA) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+} // namespace
+
+size_t tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_BYTES + sizeof(Bars) + 1024; }
+
+cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s)
+{
+    const size_t smem = tc_smem_bytes();
+    if (dtype == 1) {
+        cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_correlate_kernel<1><<<grid, TC_THREADS, smem, s>>>(p);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        tc_correlate_kernel<2><<<grid, TC_THREADS, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace corr

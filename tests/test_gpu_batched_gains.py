@@ -1,0 +1,185 @@
+"""Ragged batches (one persistent launch, CUDA-graph replay) and the gain
+adjoint against the FP64 oracle and finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import TOL_FP16, rel_frobenius_per_unit, to_numpy_int, to_numpy_vis
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RAGGED = [(16, 3, 256), (70, 2, 384), (130, 1, 128), (1, 2, 7), (65, 2, 0), (200, 1, 513),
+          (33, 4, 1000)]
+
+
+def make_batch(dtype):
+    xs, outs, hosts = [], [], []
+    for k, (S, C, T) in enumerate(RAGGED):
+        g = synth.rng(70, k)
+        if dtype == "ci8":
+            h = synth.int8_normal(g, (C, S, T, 2))
+            o = torch.full((C, S * (S + 1) // 2, 2, 2, 2), 0x7FFFFFFF, dtype=torch.int32,
+                           device="cuda")
+        else:
+            h = synth.to_cf16(synth.complex_normal(g, (C, S, T, 2)))
+            o = torch.full((C, S * (S + 1) // 2, 2, 2), float("nan"), dtype=torch.complex64,
+                           device="cuda")
+        x = torch.from_numpy(np.ascontiguousarray(h)).cuda()
+        if x.numel() == 0:
+            x = torch.zeros(16, dtype=x.dtype, device="cuda")
+        xs.append(x)
+        outs.append(o)
+        hosts.append(h)
+    return xs, outs, hosts
+
+
+def check_batch(dtype, outs, hosts):
+    for (S, C, T), o, h in zip(RAGGED, outs, hosts):
+        ref = oracle.correlate(h, dtype)
+        if dtype == "ci8":
+            got = to_numpy_int(o)
+            np.testing.assert_array_equal(got[..., 0], ref.real.astype(np.int64))
+            np.testing.assert_array_equal(got[..., 1], ref.imag.astype(np.int64))
+        else:
+            got = to_numpy_vis(o, "cf16")
+            assert np.isfinite(got).all()
+            assert rel_frobenius_per_unit(got, ref).max() < TOL_FP16
+
+
+@pytest.mark.parametrize("dtype", ["cf16", "ci8"])
+def test_ragged_batch_one_launch(dtype):
+    from paper_1702_00844_gb300 import Plan
+    plan = Plan(1, 1, 1, dtype=dtype, path="tensor")
+    xs, outs, hosts = make_batch(dtype)
+    plan.correlate_batched(list(zip(xs, outs)), RAGGED)
+    torch.cuda.synchronize()
+    plan.check_error()
+    check_batch(dtype, outs, hosts)
+
+
+def test_ragged_batch_graph_replay():
+    """The work list is built on the first call; later calls are captured in a
+    CUDA graph and replayed with identical results."""
+    from paper_1702_00844_gb300 import Plan
+    plan = Plan(1, 1, 1, dtype="cf16", path="tensor")
+    xs, outs, hosts = make_batch("cf16")
+    pairs = list(zip(xs, outs))
+    plan.correlate_batched(pairs, RAGGED)  # builds the work list (not captured)
+    torch.cuda.synchronize()
+    for o in outs:
+        o.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        plan.correlate_batched(pairs, RAGGED, stream=s)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    plan.check_error()
+    check_batch("cf16", outs, hosts)
+
+
+# ------------------------------------------------------------------ gains
+def gain_case(S=16, C=3, T=128, seed=80):
+    g = synth.rng(seed)
+    x = synth.complex_normal(g, (C, S, T, 2))
+    gains = (1 + synth.complex_normal(g, (C, S, 2), sigma=0.1)).astype(np.complex64)
+    M = synth.sky_model(C, S, T, g).astype(np.complex64)
+    return x, gains, M
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_gain_loss_and_gradients_vs_oracle():
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    x, gains, M = gain_case()
+    C, S, T, _ = x.shape
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    R = plan.correlate(xd)
+    loss = plan.gain_loss(R, gd, Md)
+    grad_g, grad_x = plan.gain_backward(xd, gd, Md, R=R)
+    # recompute path (no saved R) must agree
+    grad_g2, grad_x2 = plan.gain_backward(xd, gd, Md, R=None)
+    torch.cuda.synchronize()
+    plan.check_error()
+    Rref = oracle.correlate(x)
+    Lref, _ = oracle.gain_loss(Rref, gains, M)
+    gref = oracle.gain_grad(Rref, gains, M)
+    xref = oracle.input_grad(x, Rref, gains, M)
+    assert abs(float(loss) - Lref) < 1e-5 * Lref
+    for got, ref in ((grad_g, gref), (grad_g2, gref), (grad_x, xref), (grad_x2, xref)):
+        got = got.cpu().numpy().astype(np.complex128)
+        assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def test_gain_gradient_vs_finite_differences():
+    """GPU dL/dg against FP64 central differences of the oracle's loss."""
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    x, gains, M = gain_case(S=6, C=2, T=64, seed=81)
+    C, S, T, _ = x.shape
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    grad_g, _ = plan.gain_backward(xd, gd, Md, input_grad=False)
+    torch.cuda.synchronize()
+    Rref = oracle.correlate(x)
+    g64 = gains.astype(np.complex128)
+    fd = np.zeros_like(g64)
+    h = 1e-6
+    flat = g64.reshape(-1)
+    for k in range(flat.size):
+        for unit in (1.0, 1j):
+            gp = flat.copy(); gm = flat.copy()
+            gp[k] += h * unit
+            gm[k] -= h * unit
+            d = (oracle.gain_loss(Rref, gp.reshape(g64.shape), M)[0]
+                 - oracle.gain_loss(Rref, gm.reshape(g64.shape), M)[0]) / (2 * h)
+            fd.reshape(-1)[k] += d * unit
+    got = grad_g.cpu().numpy().astype(np.complex128)
+    assert np.abs(got - fd).max() < 1e-4 * np.abs(fd).max()
+
+
+def test_autograd_function_matches_oracle():
+    from paper_1702_00844_gb300 import FLAG_GAINS, GainCalibrationLoss, Plan
+    x, gains, M = gain_case(S=20, C=2, T=96, seed=82)
+    C, S, T, _ = x.shape
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd = _dev(x).requires_grad_(True)
+    gd = _dev(gains).requires_grad_(True)
+    Md = _dev(M)
+    L = GainCalibrationLoss.apply(xd, gd, Md, plan)
+    (3.0 * L).backward()
+    torch.cuda.synchronize()
+    Rref = oracle.correlate(x)
+    gref = 3.0 * oracle.gain_grad(Rref, gains, M)
+    xref = 3.0 * oracle.input_grad(x, Rref, gains, M)
+    got_g = gd.grad.cpu().numpy().astype(np.complex128)
+    got_x = xd.grad.cpu().numpy().astype(np.complex128)
+    assert np.abs(got_g - gref).max() < 1e-4 * np.abs(gref).max()
+    assert np.abs(got_x - xref).max() < 1e-4 * np.abs(xref).max()
+
+
+def test_differentiation_workload_full_size():
+    """64 stations, 64 channels, 1024 samples: loss and gradients against the
+    oracle's closed form on sampled channels."""
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    d = synth.differentiation()
+    x, gains, M = d["x"], d["g"], d["M"]
+    C, S, T = d["C"], d["S"], d["T"]
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    R = plan.correlate(xd)
+    grad_g, grad_x = plan.gain_backward(xd, gd, Md, R=R)
+    torch.cuda.synchronize()
+    for c in (0, 31, 63):
+        Rref = oracle.correlate(x[c][None])
+        gref = oracle.gain_grad(Rref, gains[c][None], M[c][None])
+        xref = oracle.input_grad(x[c][None], Rref, gains[c][None], M[c][None])
+        gg = grad_g[c].cpu().numpy().astype(np.complex128)[None]
+        gx = grad_x[c].cpu().numpy().astype(np.complex128)[None]
+        assert np.abs(gg - gref).max() < 1e-4 * np.abs(gref).max()
+        assert np.abs(gx - xref).max() < 1e-4 * np.abs(xref).max()
