@@ -101,7 +101,8 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out);
  * correlation formula; Fig. 2). d_in: input samples, layout and type as
  * above, n_integrations*n_channels*n_stations*n_samples*2 complex values;
  * d_out: visibilities, n_integrations*n_channels*S(S+1)/2*4 complex values,
- * fully overwritten. Asynchronous on stream; capturable in a CUDA graph. */
+ * fully overwritten. d_in may be NULL when n_samples is 0 (the output is
+ * then all zeros). Asynchronous on stream; capturable in a CUDA graph. */
 corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream);
 
 /* Correlates a ragged batch of n_sub independent sub-arrays (each with its

@@ -293,8 +293,8 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
 
 corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream)
 {
-    if (!h || !d_in || !d_out) return CORR_ERR_INVALID_ARG;
-    if (!aligned16(d_in) || !aligned16(d_out)) return CORR_ERR_INVALID_ARG;
+    if (!h || !d_out || !aligned16(d_out)) return CORR_ERR_INVALID_ARG;
+    if (h->d.n_samples > 0 && (!d_in || !aligned16(d_in))) return CORR_ERR_INVALID_ARG;
     return launch_correlate(h, d_in, d_out, static_cast<cudaStream_t>(stream));
 }
 
@@ -306,9 +306,10 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     if (n_sub == 0) return CORR_OK;
     for (int i = 0; i < n_sub; ++i) {
         const corr_subarray_t &s = subs[i];
-        if (s.n_stations < 1 || s.n_channels < 1 || s.n_samples < 0 || s.reserved != 0 || !s.d_in ||
-            !s.d_out || !aligned16(s.d_in) || !aligned16(s.d_out))
+        if (s.n_stations < 1 || s.n_channels < 1 || s.n_samples < 0 || s.reserved != 0 ||
+            !s.d_out || !aligned16(s.d_out))
             return CORR_ERR_INVALID_ARG;
+        if (s.n_samples > 0 && (!s.d_in || !aligned16(s.d_in))) return CORR_ERR_INVALID_ARG;
         if (h->d.dtype == CORR_CI8 && s.n_samples > 65535) return CORR_ERR_UNSUPPORTED;
         if (s.n_stations > 65535) return CORR_ERR_UNSUPPORTED;
     }
