@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Correlator benchmark on GB300.
+
+Headline: correlator TOPS of the tcgen05 tensor path on the precision
+workload (256 stations, 2 pols, 480 channels, 1024 samples per integration,
+complex int8 samples, bit-exact INT32 visibilities), one kernel launch per
+step, inputs resident in HBM. The same run also times the FP16 tensor path
+and the FP32 CUDA-core path on the same samples, the production FP32
+workload, the ragged batch and the gain adjoint, and reports the roofline
+of the dominant kernel, clocks during the timed region, an end-to-end figure
+with host buffers, and the FP64 CPU oracle on a bounded sample.
+
+Correlator ops = 32 per baseline per sample (8 per complex multiply-add,
+4 polarisation pairs), baselines S(S+1)/2 (Section 2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+S3, C3, T3 = 256, 480, 1024
+METRIC = "correlator TOPS & % of roofline: FP32 vs INT8/FP16 tensor path, same GB300"
+UNIT = "TOPS"
+WORKLOAD = ("precision: 256 stations, 2 pols, 480 channels, 1024 samples per integration, "
+            "complex int8 N(0,32^2) clipped to +-127, INT32 visibilities (bit-exact)")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tc_correlate_int8_precision.txt")
+TC_SOURCES = [os.path.join(ROOT, "paper_1702_00844_gb300", "csrc", f)
+              for f in ("corr_tc.cu", "ptx.cuh", "corr_internal.h")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the FP16/FP32/batch/adjoint side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def ops_of(S, T, units):
+    return 32.0 * S * (S + 1) / 2 * T * units
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- profile data
+def tc_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in TC_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None if the summary is absent or the kernel changed since."""
+    try:
+        kv = {}
+        for ln in open(PROFILE_SUMMARY):
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != tc_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------- oracle
+def oracle_sample(n_channels: int):
+    """Times the FP64 oracle on the first n_channels channels of the precision
+    workload (host data). Returns (TOPS, seconds, threads)."""
+    import oracle
+    import synth
+    d = synth.precision(channels=list(range(n_channels)))
+    t0 = time.perf_counter()
+    oracle.correlate(d["x"], "ci8")
+    dt = time.perf_counter() - t0
+    return ops_of(S3, T3, n_channels) / dt / 1e12, dt, oracle.threads()
+
+
+def cpu_baseline(target_s: float = 12.0):
+    import oracle
+    nthr = oracle.threads()
+    tops, dt, _ = oracle_sample(max(1, nthr))
+    n = max(1, nthr)
+    if dt < target_s / 3:
+        n = int(max(1, nthr) * min(8, max(1.0, target_s / max(dt, 1e-3))))
+        n = max(1, (n // nthr) * nthr) if n >= nthr else n
+        n = min(n, C3)
+        tops, dt, _ = oracle_sample(n)
+    return {"value": tops, "unit": UNIT, "cores": nthr, "kind": "oracle",
+            "sample": f"{n} of 480 channels of the precision workload (all 32896 baselines x 4 "
+                      f"pol pairs x 1024 samples each), FP64, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    nthr = oracle.threads()
+    n = max(1, nthr)
+    oracle_sample(n)  # warm-up: page in the oracle and the sample
+    times = []
+    for _ in range(args.steps):
+        tops, dt, _ = oracle_sample(n)
+        times.append(dt)
+    total = sum(times)
+    value = ops_of(S3, T3, n) * len(times) / total / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_channels_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                         "sample": f"{n} channels of the precision workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def time_launches(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps  # ms
+
+
+def secondary(x8, torch):
+    """Side measurements on one GPU: FP16 and FP32 paths on the same samples,
+    the production FP32 workload, the ragged batch and the gain adjoint."""
+    import synth
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    res = {}
+    st = torch.cuda.current_stream()
+    ops3 = ops_of(S3, T3, C3)
+    x16 = x8.to(torch.float16)
+    p16 = Plan(S3, C3, T3, dtype="cf16", path="tensor")
+    o16 = p16.empty_out()
+    ms = time_launches(lambda: p16.correlate(x16, o16), 10, 3, st)
+    res["tensor_fp16_precision"] = {"ms": ms, "TOPS": ops3 / ms / 1e9}
+    del o16, x16, p16
+    xc = torch.view_as_complex(x8.to(torch.float32).contiguous())
+    p32 = Plan(S3, C3, T3, dtype="cf32", path="fp32")
+    o32 = p32.empty_out()
+    ms = time_launches(lambda: p32.correlate(xc, o32), 3, 1, st)
+    res["fp32_cuda_core_precision"] = {"ms": ms, "TOPS": ops3 / ms / 1e9}
+    del o32, xc, p32
+    torch.cuda.empty_cache()
+    # production FP32 workload: 64 stations, 256 channels, 768 samples, 10 integrations
+    S2, C2, T2, I2 = 64, 256, 768, 10
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 2)
+    x2 = torch.randn((I2, C2, S2, T2, 2), dtype=torch.complex64, device="cuda", generator=gen)
+    p2 = Plan(S2, C2, T2, I2, dtype="cf32", path="fp32")
+    o2 = p2.empty_out()
+    ms = time_launches(lambda: p2.correlate(x2, o2), 5, 2, st)
+    res["fp32_cuda_core_production"] = {"ms": ms, "TOPS": ops_of(S2, T2, C2 * I2) / ms / 1e9}
+    del x2, o2, p2
+    torch.cuda.empty_cache()
+    # ragged batch: 32 sub-arrays, one persistent launch (graph replay)
+    shapes = synth.batching_shapes()
+    xs, outs = [], []
+    for k, (S, C, T) in enumerate(shapes):
+        xs.append(synth.batching_subarray_device(S, C, T, k, "cuda"))
+        outs.append(torch.empty((C, S * (S + 1) // 2, 2, 2), dtype=torch.complex64, device="cuda"))
+    pb = Plan(1, 1, 1, dtype="cf16", path="tensor")
+    pairs = list(zip(xs, outs))
+    pb.correlate_batched(pairs, shapes)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pb.correlate_batched(pairs, shapes, stream=s)
+    ms = time_launches(g.replay, 5, 2, torch.cuda.current_stream())
+    opsb = sum(ops_of(S, T, C) for S, C, T in shapes)
+    res["tensor_fp16_ragged_batch"] = {"ms": ms, "TOPS": opsb / ms / 1e9, "ops": opsb,
+                                       "input_GB": sum(x.numel() * 2 for x in xs) / 1e9}
+    pb.check_error()
+    del xs, outs, pairs, g, pb
+    torch.cuda.empty_cache()
+    # gain adjoint: 64 stations, 64 channels, 1024 samples
+    d = synth.differentiation()
+    pg = Plan(d["S"], d["C"], d["T"], dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd = torch.from_numpy(d["x"]).cuda()
+    gd = torch.from_numpy(d["g"]).cuda()
+    Md = torch.from_numpy(d["M"]).cuda()
+    R = pg.correlate(xd)
+    gg = torch.empty_like(gd)
+    gx = torch.empty_like(xd)
+
+    def step():
+        pg.correlate(xd, R)
+        pg.gain_backward(xd, gd, Md, R=R)
+
+    ms = time_launches(step, 10, 3, st)
+    res["gain_forward_backward_differentiation"] = {"ms": ms}
+    return res
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1702_00844_gb300 import Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+
+    x8 = synth.precision_device(C3, S3, T3, "cuda", rank=rank)
+    plan = Plan(S3, C3, T3, dtype="ci8", path="tensor")
+    out = plan.empty_out()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.correlate(x8, out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.check_error()
+    ms_step = ms_total / args.steps
+    ops = ops_of(S3, T3, C3)
+    value = ops * world * args.steps / (ms_total * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # samples from pinned memory, the correlation, D2H of the visibilities
+    xh = x8.cpu().pin_memory()
+    oh = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        x8.copy_(xh, non_blocking=True)
+        step()
+        oh.copy_(out, non_blocking=True)
+
+    e2e_ms = time_launches(e2e_step, e2e_steps, 1, stream)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": ops * world / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+           "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+           "d2h_bytes_per_step": oh.numel() * oh.element_size(), "ms_per_step": e2e_ms}
+    del xh, oh
+
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = ops / (ms_step * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(),
+            "kernel": "tc_correlate_kernel<int8>",
+            "peak_source": f"{peak_src} bf16 dense burst (f16 dense runs at the bf16 rate)",
+            "algorithmic_bytes": C3 * (S3 * T3 * 4 + S3 * (S3 + 1) // 2 * 32),
+            "hbm_bound_TOPS": ops / (C3 * (S3 * T3 * 4 + S3 * (S3 + 1) // 2 * 32)
+                                     / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)) / 1e12}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "s8",
+            "data": "synthetic (seeded device Philox, same recipe as the precision workload)",
+            "config": {"workload": WORKLOAD, "stations": S3, "pols": 2, "channels": C3,
+                       "samples": T3, "path": "tcgen05 kind::f16 with exact int8->f16 widening, "
+                       "512-sample chunks folded to INT32",
+                       "l2": "inputs 503 MB and outputs 505 MB exceed L2 (129 MB): no flush",
+                       "parallelism": f"channels per GPU fixed, {world} GPU(s), no collective"},
+            "clocks": clk.summary(), "e2e": e2e, "roofline": roof, "gpu_launches": args.steps}
+    if rank == 0 and world == 1 and not args.no_secondary:
+        line["paths"] = secondary(x8, torch)
+        fp32 = line["paths"]["fp32_cuda_core_precision"]["TOPS"]
+        line["paths"]["tensor_int8_vs_fp32_same_samples"] = value / fp32
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,10 @@ corr_status_t corr_get_error(corr_handle_t h);
 /* Static description of a status code. */
 const char *corr_status_string(corr_status_t s);
 
+/* Text of the last CUDA failure seen by this thread inside the library
+ * (empty if none). Valid until the next failing call on this thread. */
+const char *corr_last_error_message(void);
+
 /* Host-only helpers (no GPU needed), used by the plan and by tests. */
 
 /* Tile cost model of Section 2 (Table 1) for a w x h station tile:

@@ -63,6 +63,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_get_error.argtypes = [vp]
     L.corr_status_string.argtypes = [ip]
     L.corr_status_string.restype = ctypes.c_char_p
+    L.corr_last_error_message.argtypes = []
+    L.corr_last_error_message.restype = ctypes.c_char_p
     L.corr_tile_cost.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_long),
                                  ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
     L.corr_tc_tiles.argtypes = [ip]
@@ -78,7 +80,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 
 def _check(status: int, where: str):
     if status != 0:
-        raise CorrError(status, where)
+        msg = ""
+        if _LIB is not None:
+            msg = (_LIB.corr_last_error_message() or b"").decode(errors="replace")
+        raise CorrError(status, where + (f" [{msg}]" if msg else ""))
 
 
 def _stream_handle(stream) -> int:

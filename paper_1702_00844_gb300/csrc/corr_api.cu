@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -44,6 +45,8 @@ struct corr_plan {
 
 namespace {
 
+thread_local char g_last_error[256] = "";
+
 constexpr int TC_SIDE = TC_RS;
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -73,7 +76,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, int units, int tc)
 {
     auto fn = encode_fn();
-    if (!fn) return CORR_ERR_CUDA;
+    if (!fn) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled unavailable");
+        return CORR_ERR_CUDA;
+    }
     cuuint64_t dims[4] = {4, (cuuint64_t)S, (cuuint64_t)T, (cuuint64_t)units};
     cuuint64_t strides[3] = {(cuuint64_t)T * 16, 16, (cuuint64_t)S * T * 16};
     cuuint32_t box[4] = {4, 8, (cuuint32_t)tc, 1};
@@ -81,7 +87,11 @@ corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, in
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(d_in), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? CORR_OK : CORR_ERR_CUDA;
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return CORR_ERR_CUDA;
+    }
+    return CORR_OK;
 }
 
 void fp32_config(corr_plan *h)
@@ -133,6 +143,8 @@ TcProblem make_problem(const void *in, void *out, int S, int T, int units, int d
 corr_status_t cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return CORR_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return CORR_ERR_NO_MEMORY;
     return CORR_ERR_CUDA;
 }
@@ -180,6 +192,8 @@ const char *corr_status_string(corr_status_t s)
     }
     return "unknown status";
 }
+
+const char *corr_last_error_message(void) { return g_last_error; }
 
 void corr_tile_cost(int w, int h, long *flops, long *bytes, long *regs)
 {

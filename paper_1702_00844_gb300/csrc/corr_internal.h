@@ -30,11 +30,10 @@ enum TcVariant { TC_N128 = 0 };
 
 constexpr int TC_RS = 64;      // stations per tile side
 constexpr int TC_KB_T = 32;    // time samples per K-block
-constexpr int TC_STAGES = 6;
 constexpr int TC_THREADS = 13 * 32;
 constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 
-size_t tc_smem_bytes();
+size_t tc_smem_bytes(int dtype);
 cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s);
 
 // ------------------------------------------------------------------ FP32 path

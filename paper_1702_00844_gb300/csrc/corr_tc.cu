@@ -18,10 +18,14 @@
 // share of the (problem, channel, tile) list.
 //
 // Warp roles (416 threads):
-//   warps 0-7  : load samples (coalesced 16-byte loads), widen int8 to f16
-//                exactly, split polarisations and real/imaginary parts, and
-//                store both operand tiles in the 128-byte swizzled K-major
-//                layout of a ring of shared-memory stages;
+//   warps 0-7  : stage raw samples with 16-byte asynchronous copies into a
+//                per-thread ring in shared memory (each thread later converts
+//                exactly the bytes it copied, so the ring needs no barrier),
+//                widen int8 to f16 exactly, split polarisations and
+//                real/imaginary parts, and store both operand tiles in the
+//                128-byte swizzled K-major layout of a ring of operand stages.
+//                (Loads into registers would be drained by every release
+//                arrive on the stage barrier; asynchronous copies are not.)
 //   warps 8-11 : epilogue: TMEM -> registers, mask s1 <= s2, store
 //                [channel][baseline][p1][p2] once (int8: fold each 512-sample
 //                chunk into INT32 exactly);
@@ -37,14 +41,29 @@ namespace {
 
 constexpr int TILE_BYTES = 128 * 128;        // 128 rows x 128 B
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B operand tiles
-constexpr int N_PRODUCERS = 256;
+
+// Per input type: operand stages, raw stages, bytes of one unit of raw
+// samples (8 times of one station, both pols).
+template <int DT> struct Cfg;
+template <> struct Cfg<1> { static constexpr int OPS = 3, RAW = 3, RAWU = 64; };
+template <> struct Cfg<2> { static constexpr int OPS = 4, RAW = 5, RAWU = 32; };
+// 13 warps: 8 producers, 4 epilogue (one per TMEM lane quarter), 1 MMA.
+constexpr int N_PROD_WARPS = 8;
+constexpr int N_PRODUCERS = N_PROD_WARPS * 32;   // 256
 constexpr int N_EPILOGUE = 128;
 constexpr int WARP_MMA = 12;
+static_assert(TC_THREADS == 13 * 32, "warp roles");
+
+template <int DT> __host__ __device__ constexpr int raw_stage_bytes() { return 2 * Cfg<DT>::RAWU * N_PRODUCERS; }
+template <int DT> __host__ __device__ constexpr int smem_bytes()
+{
+    return Cfg<DT>::OPS * STAGE_BYTES + Cfg<DT>::RAW * raw_stage_bytes<DT>();
+}
 constexpr uint32_t TMEM_COLS = 512;
 
 struct Bars {
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
+    uint64_t full[4];
+    uint64_t empty[4];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t fin;
@@ -61,40 +80,45 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Loads samples t0..t0+7 of station s (zeros outside [0,S) x [0,T)).
+// Issues the asynchronous copy of samples t0..t0+7 of station s into the
+// unit's slot: NQ chunks of 16 bytes at dst, dst + chunk_stride, ...
+// Samples outside [0,S) x [0,T) are zero-filled. With vec (rows of whole
+// 16-byte chunks) 16-byte copies are used, otherwise one copy per sample.
 template <int DT>
-__device__ __forceinline__ void load_raw(const uint8_t *unit_in, int S, int T, bool vec, int s,
-                                         int t0, Raw<DT> &r)
+__device__ __forceinline__ void issue_raw(const uint8_t *unit_in, int S, int T, bool vec, int s,
+                                          int t0, uint32_t dst, uint32_t chunk_stride)
 {
-    constexpr int BPT = DT == 1 ? 8 : 4; // bytes per time sample (2 pols, re+im)
+    constexpr int BPT = DT == 1 ? 8 : 4;     // bytes per time sample (2 pols, re+im)
+    constexpr int NQ = Cfg<DT>::RAWU / 16;
+    constexpr int TPQ = 16 / BPT;            // samples per 16-byte chunk
+    const bool srow = s < S;
+    const uint8_t *row = unit_in + (srow ? (size_t)s * T * BPT : 0);
+    if (vec) {
 #pragma unroll
-    for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q) r.v[q] = make_uint4(0, 0, 0, 0);
-    if (s >= S || t0 >= T) return;
-    const uint8_t *p = unit_in + ((size_t)s * T + t0) * BPT;
-    if (vec && t0 + 8 <= T) {
-#pragma unroll
-        for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q)
-            r.v[q] = __ldg(reinterpret_cast<const uint4 *>(p) + q);
-        return;
-    }
-    uint32_t w[sizeof(Raw<DT>) / 4];
-#pragma unroll
-    for (int i = 0; i < (int)(sizeof(Raw<DT>) / 4); ++i) w[i] = 0;
-#pragma unroll
-    for (int tt = 0; tt < 8; ++tt) {
-        if (t0 + tt < T) {
-            if (DT == 1) {
-                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p + tt * 8));
-                w[2 * tt] = u.x;
-                w[2 * tt + 1] = u.y;
-            } else {
-                w[tt] = __ldg(reinterpret_cast<const uint32_t *>(p + tt * 4));
-            }
+        for (int q = 0; q < NQ; ++q) {
+            const int tq = t0 + q * TPQ;
+            int nb = srow ? (T - tq) * BPT : 0;
+            nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+            cp_async16(dst + q * chunk_stride, nb ? row + (size_t)tq * BPT : unit_in, (uint32_t)nb);
         }
-    }
+    } else {
 #pragma unroll
-    for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q)
-        r.v[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int i = 0; i < TPQ; ++i) {
+                const int tt = t0 + q * TPQ + i;
+                const uint32_t nb = (srow && tt < T) ? BPT : 0;
+                cp_async_small<BPT>(dst + q * chunk_stride + i * BPT,
+                                    nb ? row + (size_t)tt * BPT : unit_in, nb);
+            }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void read_raw(uint32_t src, uint32_t chunk_stride, Raw<DT> &r)
+{
+#pragma unroll
+    for (int q = 0; q < Cfg<DT>::RAWU / 16; ++q) r.v[q] = lds128(src + q * chunk_stride);
 }
 
 // Two int8 (as the low bytes of the two halves of u) -> two exact f16:
@@ -153,7 +177,7 @@ __device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&
 // 128-byte swizzled layout. The order of the four stores alternates with the
 // station parity so that each quarter-warp hits 8 distinct 16-byte bank groups.
 template <int DT>
-__device__ __forceinline__ void store_tile(uint8_t *tile, int sl, int g, const Raw<DT> &r)
+__device__ __forceinline__ void store_tile(uint32_t tile, int sl, int g, const Raw<DT> &r)
 {
     uint4 re[2], im[2];
     split<DT>(r, re, im);
@@ -163,8 +187,7 @@ __device__ __forceinline__ void store_tile(uint8_t *tile, int sl, int g, const R
         const int part = (k ^ sl) & 1;
         const int row = 2 * sl + p;
         const int chunk = g + 4 * part;
-        uint4 v = part ? im[p] : re[p];
-        *reinterpret_cast<uint4 *>(tile + row * 128 + ((chunk ^ (row & 7)) << 4)) = v;
+        sts128(tile + row * 128 + ((chunk ^ (row & 7)) << 4), part ? im[p] : re[p]);
     }
 }
 
@@ -195,7 +218,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *tiles = smem;
-    Bars *bars = reinterpret_cast<Bars *>(smem + TC_STAGES * STAGE_BYTES);
+    constexpr int OPS = Cfg<DT>::OPS;
+    constexpr int RAW = Cfg<DT>::RAW;
+    const uint32_t raw_base = smem_u32(smem + OPS * STAGE_BYTES);
+    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT>());
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x;
@@ -203,7 +229,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     const int lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < OPS; ++s) {
             mbar_init(&bars->full[s], N_PRODUCERS);
             mbar_init(&bars->empty[s], 1);
         }
@@ -224,11 +250,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     tc_fence_after();
     const uint32_t tmem_base = bars->tmem_base;
 
-    if (warp < 8) {
+    if (warp < N_PROD_WARPS) {
         // ------------------------------------------------------ producers
-        const int pt = tid;          // 0..255
-        const int sl = pt >> 2;      // station within the tile
-        const int g = pt & 3;        // group of 8 samples within the K-block
+        // Units per K-block: (operand, station-local sl, group g of 8
+        // samples); thread pt owns unit pt of A and unit pt of B.
+        const int pt = tid;
+        const int sl = pt >> 2;
+        const int g = pt & 3;
+        constexpr uint32_t CHUNK = 16 * N_PRODUCERS;                  // stride between chunks
+        constexpr uint32_t SLOT = (Cfg<DT>::RAWU / 16) * CHUNK;         // one unit slot
         int stage = 0;
         uint32_t phase = 0;
         for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
@@ -238,47 +268,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             const uint8_t *unit_in = static_cast<const uint8_t *>(P.in) +
                                      (size_t)item.unit * (size_t)P.in_unit_bytes;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
+            const bool vec = P.vec != 0;
             const int sa = item.rb * TC_RS + sl;
             const int sb = item.cb * TC_RS + sl;
-            const bool vec = P.vec != 0;
-            Raw<DT> ra[2], rbv[2];
-            load_raw<DT>(unit_in, P.S, P.T, vec, sa, 8 * g, ra[0]);
-            if (!diag) load_raw<DT>(unit_in, P.S, P.T, vec, sb, 8 * g, rbv[0]);
+            auto slot_addr = [&](int k, int j) {
+                return raw_base + (uint32_t)((k % RAW) * 2 + j) * SLOT + (uint32_t)pt * 16u;
+            };
+            auto issue_kb = [&](int k) {
+                if (k < nkb) {
+                    issue_raw<DT>(unit_in, P.S, P.T, vec, sa, k * TC_KB_T + 8 * g, slot_addr(k, 0), CHUNK);
+                    if (!diag)
+                        issue_raw<DT>(unit_in, P.S, P.T, vec, sb, k * TC_KB_T + 8 * g, slot_addr(k, 1),
+                                      CHUNK);
+                }
+                cp_async_commit(); // one group per K-block (empty past the end)
+            };
+#pragma unroll 1
+            for (int q = 0; q < RAW - 1; ++q) issue_kb(q);
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; kb += 2) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = kb + h;
-                    if (k < nkb) {
-                        if (k + 1 < nkb) {
-                            load_raw<DT>(unit_in, P.S, P.T, vec, sa, (k + 1) * TC_KB_T + 8 * g,
-                                         ra[h ^ 1]);
-                            if (!diag)
-                                load_raw<DT>(unit_in, P.S, P.T, vec, sb,
-                                             (k + 1) * TC_KB_T + 8 * g, rbv[h ^ 1]);
-                        }
-                        if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
-                                               p.wait_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        uint8_t *st = tiles + stage * STAGE_BYTES;
-                        store_tile<DT>(st, sl, g, ra[h]);
-                        if (!diag) store_tile<DT>(st + TILE_BYTES, sl, g, rbv[h]);
-                        fence_proxy_async_smem();
-                        mbar_arrive(&bars->full[stage]);
-                        if (++stage == TC_STAGES) {
-                            stage = 0;
-                            phase ^= 1;
-                        }
-                    }
+#pragma unroll 1
+            for (int k = 0; k < nkb; ++k) {
+                issue_kb(k + RAW - 1);
+                cp_async_wait<RAW - 1>(); // this thread's copies of K-block k have landed
+                Raw<DT> ra, rbv;
+                read_raw<DT>(slot_addr(k, 0), CHUNK, ra);
+                if (!diag) read_raw<DT>(slot_addr(k, 1), CHUNK, rbv);
+                if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
+                                       p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = smem_u32(tiles) + stage * STAGE_BYTES;
+                store_tile<DT>(st, sl, g, ra);
+                if (!diag) store_tile<DT>(st + TILE_BYTES, sl, g, rbv);
+                fence_proxy_async_smem();
+                mbar_arrive(&bars->full[stage]);
+                if (++stage == OPS) {
+                    stage = 0;
+                    phase ^= 1;
                 }
             }
+            cp_async_wait<0>();
             if (!ok) break;
         }
-    } else if (warp < 12) {
+    } else if (warp < WARP_MMA) {
         // ------------------------------------------------------- epilogue
-        const int eq = warp - 8;            // TMEM lane quarter of this warp
+        const int eq = warp & 3;            // TMEM lane quarter of this warp
         const int row = eq * 32 + lane;     // A row = 2*station + pol
         const int sl = row >> 1;
         const int p1 = row & 1;
@@ -299,39 +334,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + buf * 256 + ((uint32_t)(eq * 32) << 16);
 #pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    uint32_t vre[32], vim[32];
-                    tmem_ld_32x32b_x32(taddr + cc * 32, vre);
-                    tmem_ld_32x32b_x32(taddr + 128 + cc * 32, vim);
+                for (int cc = 0; cc < 8; ++cc) {
+                    // 16 columns = 8 column stations x 2 pols, Re and Im
+                    uint32_t vre[16], vim[16];
+                    tmem_ld_32x32b_x16(taddr + cc * 16, vre);
+                    tmem_ld_32x32b_x16(taddr + 128 + cc * 16, vim);
                     tmem_wait_ld();
-                    const int s2_0 = item.cb * TC_RS + cc * 16;
+                    const int s2_0 = item.cb * TC_RS + cc * 8;
+                    const long long unit_off = (long long)item.unit * P.out_unit_elems + p1 * 2;
+                    const bool last = c == nch - 1;
+                    if (DT == 1) {
+                        float2 *out = static_cast<float2 *>(P.out) + unit_off;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int s2 = s2_0 + j;
-                        if (s1 <= s2 && s2 < P.S) {
-                            const long long idx =
-                                (long long)item.unit * P.out_unit_elems +
-                                ((long long)s2 * (s2 + 1) / 2 + s1) * 4 + p1 * 2;
-                            if (DT == 1) {
-                                float4 v = make_float4(
+                        for (int j = 0; j < 8; ++j) {
+                            const int s2 = s2_0 + j;
+                            if (s1 <= s2 && s2 < P.S) {
+                                const float4 v = make_float4(
                                     __uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
-                                    __uint_as_float(vre[2 * j + 1]),
-                                    __uint_as_float(vim[2 * j + 1]));
-                                *reinterpret_cast<float4 *>(static_cast<float2 *>(P.out) + idx) = v;
-                            } else {
-                                int4 v = make_int4(__float2int_rn(__uint_as_float(vre[2 * j])),
-                                                   __float2int_rn(__uint_as_float(vim[2 * j])),
-                                                   __float2int_rn(__uint_as_float(vre[2 * j + 1])),
-                                                   __float2int_rn(__uint_as_float(vim[2 * j + 1])));
-                                int4 *dst = reinterpret_cast<int4 *>(static_cast<int2 *>(P.out) + idx);
-                                if (c > 0) {
-                                    const int4 o = *dst;
-                                    v.x += o.x;
-                                    v.y += o.y;
-                                    v.z += o.z;
-                                    v.w += o.w;
-                                }
-                                *dst = v;
+                                    __uint_as_float(vre[2 * j + 1]), __uint_as_float(vim[2 * j + 1]));
+                                st_global_cs(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4, v);
+                            }
+                        }
+                    } else {
+                        int2 *out = static_cast<int2 *>(P.out) + unit_off;
+                        int4 old[8];
+                        if (c > 0) {
+                            // fold: read every earlier partial first so the loads overlap
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int s2 = s2_0 + j;
+                                old[j] = (s1 <= s2 && s2 < P.S)
+                                             ? ld_global_cg(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4)
+                                             : make_int4(0, 0, 0, 0);
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) old[j] = make_int4(0, 0, 0, 0);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int s2 = s2_0 + j;
+                            if (s1 <= s2 && s2 < P.S) {
+                                const int4 v = make_int4(
+                                    __float2int_rn(__uint_as_float(vre[2 * j])) + old[j].x,
+                                    __float2int_rn(__uint_as_float(vim[2 * j])) + old[j].y,
+                                    __float2int_rn(__uint_as_float(vre[2 * j + 1])) + old[j].z,
+                                    __float2int_rn(__uint_as_float(vim[2 * j + 1])) + old[j].w);
+                                int2 *dst = out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4;
+                                if (last)
+                                    st_global_cs(dst, v);
+                                else
+                                    st_global_cg(dst, v);
                             }
                         }
                     }
@@ -392,7 +445,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                         tc_commit(&bars->empty[stage]);
                     }
                     __syncwarp();
-                    if (++stage == TC_STAGES) {
+                    if (++stage == OPS) {
                         stage = 0;
                         phase ^= 1;
                     }
@@ -419,11 +472,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
 
 } // namespace
 
-size_t tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_BYTES + sizeof(Bars) + 1024; }
+size_t tc_smem_bytes(int dtype)
+{
+    return (size_t)(dtype == 1 ? smem_bytes<1>() : smem_bytes<2>()) + sizeof(Bars) + 1024;
+}
 
 cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s)
 {
-    const size_t smem = tc_smem_bytes();
+    const size_t smem = tc_smem_bytes(dtype);
     if (dtype == 1) {
         cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
