@@ -14,7 +14,7 @@
 //
 // Work is a triangular schedule of 64x64-station tiles (row block <= column
 // block, Section 2's tiling of the correlation triangle; blocks of stations as
-// for large station counts in Section 5): a persistent CTA per SM walks its
+// for large station counts in Section 4.5): a persistent CTA per SM walks its
 // share of the (problem, channel, tile) list.
 //
 // Warp roles (416 threads):

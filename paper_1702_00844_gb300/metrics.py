@@ -14,13 +14,13 @@ def correlator_ops(S: int, T: int, units: int) -> float:
 
 
 def ai_global(S: int) -> float:
-    """Global arithmetic intensity of FP32 input (Section 4): 32 flops per
+    """Global arithmetic intensity of FP32 input (Section 3.6): 32 flops per
     baseline over 16 bytes per station per sample = S + 1."""
     return 32.0 * n_baselines(S) / (16.0 * S)
 
 
 def perf_max(peak: float, ai: float, bandwidth: float) -> float:
-    """Bound-and-bottleneck model (Section 4): min(peak, AI x bandwidth)."""
+    """Bound-and-bottleneck model (Section 3.6): min(peak, AI x bandwidth)."""
     return min(peak, ai * bandwidth)
 
 

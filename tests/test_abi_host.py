@@ -121,7 +121,7 @@ def test_roofline_examples_from_the_paper():
 
 
 def test_global_arithmetic_intensity():
-    """AI_global = nrStations + 1 (Section 4): 32 flops per baseline over 16
+    """AI_global = nrStations + 1 (Section 3.6): 32 flops per baseline over 16
     bytes per station per sample."""
     from paper_1702_00844_gb300.metrics import ai_global, correlator_ops
     assert ai_global(64) == 65
