@@ -39,6 +39,8 @@
 #ifndef CORR_H
 #define CORR_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -156,6 +158,37 @@ const char *corr_status_string(corr_status_t s);
 /* Text of the last CUDA failure seen by this thread inside the library
  * (empty if none). Valid until the next failing call on this thread. */
 const char *corr_last_error_message(void);
+
+/* corr_gain_backward without a plan and without any allocation.
+ *
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc, such as a real-time pipeline that forbids allocation once
+ * observing has started, a plug-in running inside another framework's
+ * memory pool, or code issuing work where an allocation would synchronize
+ * the device. It computes what corr_gain_backward computes (same gradient
+ * convention and layouts) for n_units channels of n_stations stations and
+ * n_samples samples, with d_raw_vis (R from corr_correlate) required.
+ *
+ * Scratch (the input-gradient matrix W', 16*S*S*n_units bytes when
+ * d_grad_in is given, and one float per channel when d_loss is given) lives
+ * in a fixed array of corr_noalloc_scratch_bytes() bytes (16 MiB) that the
+ * library holds on every GPU that loads it, until the process exits. Larger
+ * problems are rejected with CORR_ERR_UNSUPPORTED and a message in
+ * corr_last_error_message. Nothing in the array needs to start at zero;
+ * every call overwrites what it uses. The first call on a device looks up
+ * the array's device address with that device current (a synchronous
+ * runtime call), so make it before any stream capture. All calls share the
+ * one array: calls whose kernels overlap on the GPU (different streams
+ * without ordering) race and give wrong results. No cudaMalloc, cudaFree or
+ * allocating library routine is called. Asynchronous on stream. */
+corr_status_t corr_gain_backward_noalloc(int n_stations, int n_units, int n_samples,
+                                         const void *d_in, const void *d_gain,
+                                         const void *d_vis_model, const void *d_raw_vis,
+                                         void *d_grad_gain, void *d_grad_in, float *d_loss,
+                                         const float *d_grad_scale, void *stream);
+
+/* Size in bytes of the fixed scratch array of corr_gain_backward_noalloc. */
+size_t corr_noalloc_scratch_bytes(void);
 
 /* Host-only helpers (no GPU needed), used by the plan and by tests. */
 

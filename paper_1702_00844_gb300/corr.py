@@ -71,6 +71,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_tc_tile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_fp32_subtiles.argtypes = [ip]
     L.corr_fp32_subtile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.corr_gain_backward_noalloc.argtypes = [ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.corr_gain_backward_noalloc.restype = ip
+    L.corr_noalloc_scratch_bytes.argtypes = []
+    L.corr_noalloc_scratch_bytes.restype = ctypes.c_size_t
     for name in ("corr_create", "corr_correlate", "corr_correlate_batched", "corr_gain_loss",
                  "corr_gain_backward", "corr_destroy", "corr_get_error"):
         getattr(L, name).restype = ip

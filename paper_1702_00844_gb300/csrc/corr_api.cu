@@ -178,6 +178,13 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
 
 } // namespace
 
+void corr::set_last_error(cudaError_t e)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void corr::set_last_error(const char *msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 extern "C" {
 
 const char *corr_status_string(corr_status_t s)

@@ -59,4 +59,8 @@ cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
                               const float2 *M, const float *scale, float2 *W,
                               float2 *grad_x, int S, int T, int units, cudaStream_t s);
 
+// Records the text returned by corr_last_error_message on this thread.
+void set_last_error(cudaError_t e);
+void set_last_error(const char *msg);
+
 } // namespace corr
