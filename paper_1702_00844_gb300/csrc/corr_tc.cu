@@ -44,9 +44,25 @@ constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B operand tiles
 
 // Per input type: operand stages, raw stages, bytes of one unit of raw
 // samples (8 times of one station, both pols).
+#ifndef CORR_TC_OPS_F16
+#define CORR_TC_OPS_F16 3
+#endif
+#ifndef CORR_TC_RAW_F16
+#define CORR_TC_RAW_F16 3
+#endif
+#ifndef CORR_TC_OPS_I8
+#define CORR_TC_OPS_I8 4
+#endif
+#ifndef CORR_TC_RAW_I8
+#define CORR_TC_RAW_I8 5
+#endif
+constexpr int MAX_OPS = 4; // size of the stage barrier arrays
 template <int DT> struct Cfg;
-template <> struct Cfg<1> { static constexpr int OPS = 3, RAW = 3, RAWU = 64; };
-template <> struct Cfg<2> { static constexpr int OPS = 4, RAW = 5, RAWU = 32; };
+template <> struct Cfg<1> { static constexpr int OPS = CORR_TC_OPS_F16, RAW = CORR_TC_RAW_F16, RAWU = 64; };
+template <> struct Cfg<2> { static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, RAWU = 32; };
+static_assert(Cfg<1>::OPS >= 2 && Cfg<1>::OPS <= MAX_OPS && Cfg<2>::OPS >= 2 && Cfg<2>::OPS <= MAX_OPS,
+              "operand stages must fit the barrier arrays");
+static_assert(Cfg<1>::RAW >= 2 && Cfg<2>::RAW >= 2, "at least two raw stages");
 // 13 warps: 8 producers, 4 epilogue (one per TMEM lane quarter), 1 MMA.
 constexpr int N_PROD_WARPS = 8;
 constexpr int N_PRODUCERS = N_PROD_WARPS * 32;   // 256
@@ -62,8 +78,8 @@ template <int DT> __host__ __device__ constexpr int smem_bytes()
 constexpr uint32_t TMEM_COLS = 512;
 
 struct Bars {
-    uint64_t full[4];
-    uint64_t empty[4];
+    uint64_t full[MAX_OPS];
+    uint64_t empty[MAX_OPS];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t fin;
@@ -80,23 +96,31 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Issues the asynchronous copy of samples t0..t0+7 of station s into the
-// unit's slot: NQ chunks of 16 bytes at dst, dst + chunk_stride, ...
-// Samples outside [0,S) x [0,T) are zero-filled. With vec (rows of whole
-// 16-byte chunks) 16-byte copies are used, otherwise one copy per sample.
+// Issues the asynchronous copies of one unit: station s, chunks g, g+4, ...
+// (16 bytes each) of the K-block starting at sample t0, into the unit's slot
+// (chunk q at dst + q*chunk_stride). The four threads of a station thus read
+// 64 contiguous bytes per copy instruction. The unit holds 8 samples that are
+// not consecutive in time; A and B use the same assignment, so the products
+// pair the same samples. Samples outside [0,S) x [0,T) are zero-filled. With
+// vec (rows of whole 16-byte chunks) 16-byte copies are used, otherwise one
+// copy per sample.
 template <int DT>
 __device__ __forceinline__ void issue_raw(const uint8_t *unit_in, int S, int T, bool vec, int s,
-                                          int t0, uint32_t dst, uint32_t chunk_stride)
+                                          int t0, int g, uint32_t dst, uint32_t chunk_stride)
 {
     constexpr int BPT = DT == 1 ? 8 : 4;     // bytes per time sample (2 pols, re+im)
     constexpr int NQ = Cfg<DT>::RAWU / 16;
     constexpr int TPQ = 16 / BPT;            // samples per 16-byte chunk
     const bool srow = s < S;
     const uint8_t *row = unit_in + (srow ? (size_t)s * T * BPT : 0);
-    if (vec) {
+    if (vec && srow && t0 + TC_KB_T <= T) {  // whole K-block in range
+        const uint8_t *src = row + (size_t)t0 * BPT + g * 16;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) cp_async16(dst + q * chunk_stride, src + q * 64, 16u);
+    } else if (vec) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const int tq = t0 + q * TPQ;
+            const int tq = t0 + (g + 4 * q) * TPQ;
             int nb = srow ? (T - tq) * BPT : 0;
             nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
             cp_async16(dst + q * chunk_stride, nb ? row + (size_t)tq * BPT : unit_in, (uint32_t)nb);
@@ -106,7 +130,7 @@ __device__ __forceinline__ void issue_raw(const uint8_t *unit_in, int S, int T, 
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int i = 0; i < TPQ; ++i) {
-                const int tt = t0 + q * TPQ + i;
+                const int tt = t0 + (g + 4 * q) * TPQ + i;
                 const uint32_t nb = (srow && tt < T) ? BPT : 0;
                 cp_async_small<BPT>(dst + q * chunk_stride + i * BPT,
                                     nb ? row + (size_t)tt * BPT : unit_in, nb);
@@ -140,7 +164,7 @@ __device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&
 {
     uint32_t o_re[2][4], o_im[2][4];
     if (DT == 1) {
-        // word 2t+p = (re, im) of pol p at time t (low half = re)
+        // word 2t+p = (re, im) of pol p at the unit's t-th sample (low half = re)
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -152,7 +176,7 @@ __device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&
                 o_im[p][q] = __byte_perm(w0, w1, 0x7632);
             }
     } else {
-        // word t = bytes (p0 re, p0 im, p1 re, p1 im) at time t
+        // word t = bytes (p0 re, p0 im, p1 re, p1 im) of the unit's t-th sample
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -276,10 +300,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             };
             auto issue_kb = [&](int k) {
                 if (k < nkb) {
-                    issue_raw<DT>(unit_in, P.S, P.T, vec, sa, k * TC_KB_T + 8 * g, slot_addr(k, 0), CHUNK);
+                    issue_raw<DT>(unit_in, P.S, P.T, vec, sa, k * TC_KB_T, g, slot_addr(k, 0), CHUNK);
                     if (!diag)
-                        issue_raw<DT>(unit_in, P.S, P.T, vec, sb, k * TC_KB_T + 8 * g, slot_addr(k, 1),
-                                      CHUNK);
+                        issue_raw<DT>(unit_in, P.S, P.T, vec, sb, k * TC_KB_T, g, slot_addr(k, 1), CHUNK);
                 }
                 cp_async_commit(); // one group per K-block (empty past the end)
             };

@@ -59,6 +59,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// As mbar_try_wait, but the thread may be suspended for up to hint_ns
+// waiting for the phase to complete (it resumes as soon as it does).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits until the phase with the given parity of *bar has completed. Gives up
 // after limit_ns of wall time or as soon as *abort is set: then it sets
 // *abort, records ERR_WAIT_TIMEOUT in *err and returns false.
@@ -69,8 +84,8 @@ static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 0u) {
+        if (mbar_try_wait_hint(bar, parity, 2000u)) return true;
+        if ((i & 15u) == 0u) {
             if (*abort) return false;
             if (globaltimer_ns() - t0 > limit_ns) {
                 *abort = 1;
