@@ -148,6 +148,12 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
  * NULL is accepted. */
 corr_status_t corr_destroy(corr_handle_t h);
 
+/* Tile variant the plan's tensor path uses: 0 = 64x64-station tiles,
+ * 1 = 64 x up to 128 stations; -1 for FP32 plans or NULL. Chosen in
+ * corr_create by timing both (see CORR_FLAG_NO_AUTOTUNE); the environment
+ * variable CORR_TC_VARIANT=narrow|wide forces one. */
+int corr_tile_variant(corr_handle_t h);
+
 /* Reads and clears the plan's device error word (synchronous copy):
  * CORR_OK or CORR_ERR_TIMEOUT. */
 corr_status_t corr_get_error(corr_handle_t h);

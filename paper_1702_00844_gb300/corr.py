@@ -67,6 +67,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_last_error_message.restype = ctypes.c_char_p
     L.corr_tile_cost.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_long),
                                  ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
+    L.corr_tile_variant.argtypes = [vp]
+    L.corr_tile_variant.restype = ip
     L.corr_tc_tiles.argtypes = [ip]
     L.corr_tc_tile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_fp32_subtiles.argtypes = [ip]
@@ -184,6 +186,10 @@ class Plan:
         return grad_g, grad_x
 
     # ------------------------------------------------------------- misc
+    def tile_variant(self) -> str:
+        v = self.L.corr_tile_variant(self.h)
+        return {0: "narrow", 1: "wide"}.get(v, "fp32")
+
     def check_error(self):
         _check(self.L.corr_get_error(self.h), "corr_get_error")
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -32,11 +34,14 @@ struct corr_plan {
     int4 *d_items = nullptr;
     int n_items = 0;
     int tc_grid = 0;
+    int tc_variant = TC_NARROW;
+    float tune_ms[2] = {0.f, 0.f};
     // ragged batches
     std::vector<corr_subarray_t> batch_key;
     TcProblem *d_bprobs = nullptr;
     int4 *d_bitems = nullptr;
     int n_bitems = 0;
+    int b_variant = TC_NARROW;
     // gain calibration
     float2 *d_R = nullptr;     // recomputed raw visibilities
     float2 *d_W = nullptr;     // W' per channel
@@ -113,14 +118,26 @@ void fp32_config(corr_plan *h)
     h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;
 }
 
-std::vector<int4> tc_items_for(int prob, int S, int units)
+// Work items of the tensor kernel: {prob, unit, rb, cb0 | ncb << 16}, row
+// block rb and column blocks cb0..cb0+ncb-1 of 64 stations, rb <= cb0.
+// narrow: every (rb, cb) with rb <= cb; wide: column blocks taken in pairs
+// from the row block onward (the last one alone if the count is odd).
+std::vector<int4> tc_items_for(int prob, int S, int units, int variant)
 {
     std::vector<int4> v;
     const int nb = tc_blocks(S);
-    v.reserve((size_t)units * nb * (nb + 1) / 2);
-    for (int u = 0; u < units; ++u)
-        for (int cb = 0; cb < nb; ++cb)
-            for (int rb = 0; rb <= cb; ++rb) v.push_back(make_int4(prob, u, rb, cb));
+    for (int u = 0; u < units; ++u) {
+        if (variant == TC_WIDE) {
+            for (int rb = 0; rb < nb; ++rb)
+                for (int cb = rb; cb < nb; cb += 2) {
+                    const int ncb = std::min(2, nb - cb);
+                    v.push_back(make_int4(prob, u, rb, cb | (ncb << 16)));
+                }
+        } else {
+            for (int cb = 0; cb < nb; ++cb)
+                for (int rb = 0; rb <= cb; ++rb) v.push_back(make_int4(prob, u, rb, cb | (1 << 16)));
+        }
+    }
     return v;
 }
 
@@ -173,7 +190,114 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
     p.chunk_kb = d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return cuda_status(tc_launch(d.dtype, p, h->tc_grid, s));
+    return cuda_status(tc_launch(d.dtype, h->tc_variant == TC_WIDE, p, h->tc_grid, s));
+}
+
+// ------------------------------------------------------------------ autotuner
+// The tile variant of the tensor path is chosen per (device, dtype, S, T) by
+// timing both variants once on zero-filled samples of the plan's shape (about
+// four waves of work items over the SMs), unless CORR_TC_VARIANT=narrow|wide
+// forces one or CORR_FLAG_NO_AUTOTUNE asks for the heuristic (wide from 128
+// stations). Choices are cached for the process.
+struct TuneKey {
+    int dev, dtype, S, T;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dev, dtype, S, T) < std::tie(o.dev, o.dtype, o.S, o.T);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+int forced_variant()
+{
+    const char *e = std::getenv("CORR_TC_VARIANT");
+    if (!e) return -1;
+    if (std::strcmp(e, "wide") == 0) return TC_WIDE;
+    if (std::strcmp(e, "narrow") == 0) return TC_NARROW;
+    return -1;
+}
+
+corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, const void *d_in,
+                           void *d_out, float *ms_out)
+{
+    std::vector<int4> items = tc_items_for(0, S, units, variant);
+    int4 *d_items = nullptr;
+    corr_status_t st = cuda_status(cudaMalloc(&d_items, items.size() * sizeof(int4)));
+    if (st != CORR_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    do {
+        if ((st = cuda_status(cudaMemcpy(d_items, items.data(), items.size() * sizeof(int4),
+                                         cudaMemcpyHostToDevice))) != CORR_OK)
+            break;
+        TcParams p{};
+        p.prob0 = make_problem(d_in, d_out, S, T, units, h->d.dtype);
+        p.items = d_items;
+        p.n_items = (int)items.size();
+        p.chunk_kb = h->d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
+        p.err = h->d_err;
+        p.wait_ns = h->wait_ns;
+        const int grid = std::max(1, std::min(p.n_items, h->sm_count));
+        if ((st = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
+        if ((st = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
+        for (int i = 0; i < 2 && st == CORR_OK; ++i)
+            st = cuda_status(tc_launch(h->d.dtype, variant == TC_WIDE, p, grid, 0));
+        if (st != CORR_OK) break;
+        cudaEventRecord(e0, 0);
+        for (int i = 0; i < 3 && st == CORR_OK; ++i)
+            st = cuda_status(tc_launch(h->d.dtype, variant == TC_WIDE, p, grid, 0));
+        cudaEventRecord(e1, 0);
+        if (st != CORR_OK) break;
+        if ((st = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *ms_out = ms / 3.f;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_items);
+    return st;
+}
+
+corr_status_t tune_tensor_variant(corr_plan *h)
+{
+    const corr_desc_t &d = h->d;
+    const int f = forced_variant();
+    if (f >= 0) {
+        h->tc_variant = f;
+        return CORR_OK;
+    }
+    if ((d.flags & CORR_FLAG_NO_AUTOTUNE) || d.n_samples == 0) {
+        h->tc_variant = d.n_stations >= 128 ? TC_WIDE : TC_NARROW;
+        return CORR_OK;
+    }
+    const TuneKey key{h->device, d.dtype, d.n_stations, d.n_samples};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->tc_variant = it->second;
+            return CORR_OK;
+        }
+    }
+    const long long units = (long long)d.n_channels * d.n_integrations;
+    const long long per_unit = (long long)tc_blocks(d.n_stations) * (tc_blocks(d.n_stations) + 1) / 2;
+    const int su = (int)std::max(1LL, std::min(units, (4LL * h->sm_count + per_unit - 1) / per_unit));
+    const size_t in_bytes = (size_t)su * d.n_stations * d.n_samples * bytes_per_sample(d.dtype);
+    const size_t out_bytes = (size_t)su * n_baselines(d.n_stations) * 4 * 8;
+    void *d_in = nullptr, *d_out = nullptr;
+    corr_status_t st = cuda_status(cudaMalloc(&d_in, in_bytes));
+    if (st == CORR_OK) st = cuda_status(cudaMalloc(&d_out, out_bytes));
+    if (st == CORR_OK) st = cuda_status(cudaMemset(d_in, 0, in_bytes));
+    for (int v = 0; v < 2 && st == CORR_OK; ++v)
+        st = time_variant(h, v, d.n_stations, d.n_samples, su, d_in, d_out, &h->tune_ms[v]);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (st != CORR_OK) return st;
+    h->tc_variant = h->tune_ms[TC_WIDE] < h->tune_ms[TC_NARROW] ? TC_WIDE : TC_NARROW;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = h->tc_variant;
+    return CORR_OK;
 }
 
 } // namespace
@@ -288,7 +412,8 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
         if (path == CORR_PATH_FP32) {
             fp32_config(h);
         } else {
-            std::vector<int4> items = tc_items_for(0, d.n_stations, (int)units);
+            if ((st = tune_tensor_variant(h)) != CORR_OK) break;
+            std::vector<int4> items = tc_items_for(0, d.n_stations, (int)units, h->tc_variant);
             h->n_items = (int)items.size();
             if ((st = cuda_status(cudaMalloc(&h->d_items, items.size() * sizeof(int4)))) != CORR_OK)
                 break;
@@ -341,7 +466,19 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     if (!same) {
         // Build the ragged work list: tiles of all sub-arrays, heaviest (longest
         // integration) first so that the static round-robin split over the
-        // persistent CTAs ends evenly.
+        // persistent CTAs ends evenly. One tile variant serves the whole batch:
+        // wide when most of the work is in sub-arrays of >= 128 stations.
+        {
+            const int f = forced_variant();
+            double big = 0, all = 0;
+            for (int i = 0; i < n_sub; ++i) {
+                const double w = (double)n_baselines(subs[i].n_stations) * subs[i].n_samples *
+                                 subs[i].n_channels;
+                all += w;
+                if (subs[i].n_stations >= 128) big += w;
+            }
+            h->b_variant = f >= 0 ? f : (big >= 0.5 * all ? TC_WIDE : TC_NARROW);
+        }
         std::vector<TcProblem> probs;
         std::vector<int4> items;
         for (int i = 0; i < n_sub; ++i) {
@@ -349,7 +486,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
             probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
                                          h->d.dtype));
             if (s.n_samples == 0) continue;
-            std::vector<int4> v = tc_items_for(i, s.n_stations, s.n_channels);
+            std::vector<int4> v = tc_items_for(i, s.n_stations, s.n_channels, h->b_variant);
             items.insert(items.end(), v.begin(), v.end());
         }
         std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
@@ -389,7 +526,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
     const int grid = std::max(1, std::min(h->n_bitems, h->sm_count));
-    return cuda_status(tc_launch(h->d.dtype, p, grid, st));
+    return cuda_status(tc_launch(h->d.dtype, h->b_variant == TC_WIDE, p, grid, st));
 }
 
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
@@ -436,6 +573,12 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     if (d_loss)
         e = cuda_status(gain_loss_launch(R, g, M, nullptr, h->d_partial, d_loss, S, units, st));
     return e;
+}
+
+int corr_tile_variant(corr_handle_t h)
+{
+    if (!h) return -1;
+    return h->path == CORR_PATH_TENSOR ? h->tc_variant : -1;
 }
 
 corr_status_t corr_get_error(corr_handle_t h)

@@ -26,15 +26,16 @@ struct TcParams {
     unsigned long long wait_ns;
 };
 
-enum TcVariant { TC_N128 = 0 };
+// Tile variants of the tensor kernel: narrow = 64x64-station tiles (N=128,
+// double-buffered accumulators); wide = 64 x up to 128 stations (N=256).
+enum TcVariant { TC_NARROW = 0, TC_WIDE = 1 };
 
 constexpr int TC_RS = 64;      // stations per tile side
 constexpr int TC_KB_T = 32;    // time samples per K-block
 constexpr int TC_THREADS = 13 * 32;
 constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 
-size_t tc_smem_bytes(int dtype);
-cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s);
+cudaError_t tc_launch(int dtype, bool wide, const TcParams &p, int grid, cudaStream_t s);
 
 // ------------------------------------------------------------------ FP32 path
 struct Fp32Params {

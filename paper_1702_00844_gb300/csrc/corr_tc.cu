@@ -12,25 +12,28 @@
 //     Im += A[k2]B[k0] + A[k3]B[k1] - A[k0]B[k2] - A[k1]B[k3]   (negate-A bit)
 // so no rotated copy of either operand is needed.
 //
-// Work is a triangular schedule of 64x64-station tiles (row block <= column
-// block, Section 2's tiling of the correlation triangle; blocks of stations as
-// for large station counts in Section 4.5): a persistent CTA per SM walks its
-// share of the (problem, channel, tile) list.
+// Work is a triangular schedule of tiles over the correlation triangle
+// (Section 2's tiling; blocks of stations as for large station counts in
+// Section 4.5): the row block is 64 stations (M = 128 rows), the column range
+// one block of 64 stations (N = 128, "narrow") or up to two (N = 256,
+// "wide"), starting at or after the row block. A persistent CTA per SM walks
+// its share of the (problem, channel, tile) list.
 //
 // Warp roles (416 threads):
 //   warps 0-7  : stage raw samples with 16-byte asynchronous copies into a
 //                per-thread ring in shared memory (each thread later converts
 //                exactly the bytes it copied, so the ring needs no barrier),
 //                widen int8 to f16 exactly, split polarisations and
-//                real/imaginary parts, and store both operand tiles in the
+//                real/imaginary parts, and store the operand tiles in the
 //                128-byte swizzled K-major layout of a ring of operand stages.
 //                (Loads into registers would be drained by every release
 //                arrive on the stage barrier; asynchronous copies are not.)
 //   warps 8-11 : epilogue: TMEM -> registers, mask s1 <= s2, store
 //                [channel][baseline][p1][p2] once (int8: fold each 512-sample
 //                chunk into INT32 exactly);
-//   warp 12    : allocates TMEM (2 accumulator buffers x (Re 128 + Im 128)
-//                columns) and issues the MMAs (one thread).
+//   warp 12    : allocates TMEM (narrow: 2 accumulator buffers x (Re 128 +
+//                Im 128) columns; wide: 1 buffer x (Re 256 + Im 256)) and
+//                issues the MMAs (one thread).
 // Every wait is bounded (see mbar_wait_bounded).
 #include "corr_internal.h"
 #include "ptx.cuh"
@@ -39,11 +42,21 @@ namespace corr {
 
 namespace {
 
-constexpr int TILE_BYTES = 128 * 128;        // 128 rows x 128 B
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B operand tiles
+constexpr int TILE_BYTES = 128 * 128; // one operand block: 128 rows x 128 B
 
-// Per input type: operand stages, raw stages, bytes of one unit of raw
-// samples (8 times of one station, both pols).
+// 13 warps: 8 producers, 4 epilogue (one per TMEM lane quarter), 1 MMA.
+constexpr int N_PROD_WARPS = 8;
+constexpr int N_PRODUCERS = N_PROD_WARPS * 32; // 256
+constexpr int N_EPILOGUE = 128;
+constexpr int WARP_MMA = 12;
+static_assert(TC_THREADS == 13 * 32, "warp roles");
+constexpr uint32_t TMEM_COLS = 512;
+
+// Bytes of one unit of raw samples (8 times of one station, both pols).
+template <int DT> struct RawBytes { static constexpr int value = DT == 1 ? 64 : 32; };
+
+// Per input type and tile width: operand stages, raw stages, operand blocks
+// of B per tile and TMEM accumulator buffers.
 #ifndef CORR_TC_OPS_F16
 #define CORR_TC_OPS_F16 3
 #endif
@@ -57,25 +70,28 @@ constexpr int STAGE_BYTES = 2 * TILE_BYTES;  // A and B operand tiles
 #define CORR_TC_RAW_I8 5
 #endif
 constexpr int MAX_OPS = 4; // size of the stage barrier arrays
-template <int DT> struct Cfg;
-template <> struct Cfg<1> { static constexpr int OPS = CORR_TC_OPS_F16, RAW = CORR_TC_RAW_F16, RAWU = 64; };
-template <> struct Cfg<2> { static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, RAWU = 32; };
-static_assert(Cfg<1>::OPS >= 2 && Cfg<1>::OPS <= MAX_OPS && Cfg<2>::OPS >= 2 && Cfg<2>::OPS <= MAX_OPS,
-              "operand stages must fit the barrier arrays");
-static_assert(Cfg<1>::RAW >= 2 && Cfg<2>::RAW >= 2, "at least two raw stages");
-// 13 warps: 8 producers, 4 epilogue (one per TMEM lane quarter), 1 MMA.
-constexpr int N_PROD_WARPS = 8;
-constexpr int N_PRODUCERS = N_PROD_WARPS * 32;   // 256
-constexpr int N_EPILOGUE = 128;
-constexpr int WARP_MMA = 12;
-static_assert(TC_THREADS == 13 * 32, "warp roles");
+template <int DT, bool WIDE> struct Cfg;
+template <> struct Cfg<1, false> {
+    static constexpr int OPS = CORR_TC_OPS_F16, RAW = CORR_TC_RAW_F16, MAXB = 1, NBUF = 2;
+};
+template <> struct Cfg<2, false> {
+    static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, MAXB = 1, NBUF = 2;
+};
+template <> struct Cfg<1, true> { static constexpr int OPS = 2, RAW = 2, MAXB = 2, NBUF = 1; };
+template <> struct Cfg<2, true> { static constexpr int OPS = 3, RAW = 3, MAXB = 2, NBUF = 1; };
 
-template <int DT> __host__ __device__ constexpr int raw_stage_bytes() { return 2 * Cfg<DT>::RAWU * N_PRODUCERS; }
-template <int DT> __host__ __device__ constexpr int smem_bytes()
+template <int DT, bool WIDE> __host__ __device__ constexpr int stage_bytes()
 {
-    return Cfg<DT>::OPS * STAGE_BYTES + Cfg<DT>::RAW * raw_stage_bytes<DT>();
+    return (1 + Cfg<DT, WIDE>::MAXB) * TILE_BYTES;
 }
-constexpr uint32_t TMEM_COLS = 512;
+template <int DT, bool WIDE> __host__ __device__ constexpr int raw_stage_bytes()
+{
+    return (1 + Cfg<DT, WIDE>::MAXB) * RawBytes<DT>::value * N_PRODUCERS;
+}
+template <int DT, bool WIDE> __host__ __device__ constexpr int smem_bytes()
+{
+    return Cfg<DT, WIDE>::OPS * stage_bytes<DT, WIDE>() + Cfg<DT, WIDE>::RAW * raw_stage_bytes<DT, WIDE>();
+}
 
 struct Bars {
     uint64_t full[MAX_OPS];
@@ -86,6 +102,14 @@ struct Bars {
     uint32_t tmem_base;
     int abort_flag;
 };
+
+template <int DT, bool WIDE> constexpr bool cfg_ok()
+{
+    return Cfg<DT, WIDE>::OPS >= 2 && Cfg<DT, WIDE>::OPS <= MAX_OPS && Cfg<DT, WIDE>::RAW >= 2 &&
+           smem_bytes<DT, WIDE>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
+}
+static_assert(cfg_ok<1, false>() && cfg_ok<2, false>() && cfg_ok<1, true>() && cfg_ok<2, true>(),
+              "stage counts must fit the barrier arrays and shared memory");
 
 template <int DT> struct Raw;          // raw samples of 8 times of one station
 template <> struct Raw<1> { uint4 v[4]; }; // complex f16 x 2 pols: 64 bytes
@@ -109,7 +133,7 @@ __device__ __forceinline__ void issue_raw(const uint8_t *unit_in, int S, int T, 
                                           int t0, int g, uint32_t dst, uint32_t chunk_stride)
 {
     constexpr int BPT = DT == 1 ? 8 : 4;     // bytes per time sample (2 pols, re+im)
-    constexpr int NQ = Cfg<DT>::RAWU / 16;
+    constexpr int NQ = RawBytes<DT>::value / 16;
     constexpr int TPQ = 16 / BPT;            // samples per 16-byte chunk
     const bool srow = s < S;
     const uint8_t *row = unit_in + (srow ? (size_t)s * T * BPT : 0);
@@ -142,7 +166,7 @@ template <int DT>
 __device__ __forceinline__ void read_raw(uint32_t src, uint32_t chunk_stride, Raw<DT> &r)
 {
 #pragma unroll
-    for (int q = 0; q < Cfg<DT>::RAWU / 16; ++q) r.v[q] = lds128(src + q * chunk_stride);
+    for (int q = 0; q < RawBytes<DT>::value / 16; ++q) r.v[q] = lds128(src + q * chunk_stride);
 }
 
 // Two int8 (as the low bytes of the two halves of u) -> two exact f16:
@@ -215,14 +239,16 @@ __device__ __forceinline__ void store_tile(uint32_t tile, int sl, int g, const R
     }
 }
 
+// A work item: channel `unit` of problem `prob`, row block rb, column blocks
+// cb0 .. cb0 + ncb - 1 (64 stations each), packed as {prob, unit, rb, cb0 | ncb << 16}.
 struct Item {
-    int prob, unit, rb, cb;
+    int prob, unit, rb, cb0, ncb;
 };
 
 __device__ __forceinline__ Item get_item(const TcParams &p, int i)
 {
     const int4 v = __ldg(p.items + i);
-    return Item{v.x, v.y, v.z, v.w};
+    return Item{v.x, v.y, v.z, v.w & 0xFFFF, v.w >> 16};
 }
 
 __device__ __forceinline__ TcProblem get_prob(const TcParams &p, int k)
@@ -235,17 +261,23 @@ __device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
     return chunk_kb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
 }
 
-template <int DT>
+template <int DT, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
 {
+    using C = Cfg<DT, WIDE>;
+    constexpr int OPS = C::OPS;
+    constexpr int RAW = C::RAW;
+    constexpr int NBUF = C::NBUF;
+    constexpr uint32_t STAGE = stage_bytes<DT, WIDE>();
+    constexpr uint32_t IMOFF = WIDE ? 256 : 128;   // TMEM column of Im relative to Re
+    constexpr uint32_t BUFCOLS = WIDE ? 0 : 256;   // TMEM columns between buffers
+
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *tiles = smem;
-    constexpr int OPS = Cfg<DT>::OPS;
-    constexpr int RAW = Cfg<DT>::RAW;
-    const uint32_t raw_base = smem_u32(smem + OPS * STAGE_BYTES);
-    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT>());
+    const uint32_t tiles_u32 = smem_u32(smem);
+    const uint32_t raw_base = tiles_u32 + OPS * STAGE;
+    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, WIDE>());
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x;
@@ -276,33 +308,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
 
     if (warp < N_PROD_WARPS) {
         // ------------------------------------------------------ producers
-        // Units per K-block: (operand, station-local sl, group g of 8
-        // samples); thread pt owns unit pt of A and unit pt of B.
+        // Units per K-block: (operand block, station-local sl, group g of 8
+        // samples); thread pt owns unit pt of A and unit pt of each B block.
+        // Operand block slots per stage: 0 = A, 1.. = the B blocks that are
+        // not A itself (a diagonal tile reuses A as its first B block).
         const int pt = tid;
         const int sl = pt >> 2;
         const int g = pt & 3;
         constexpr uint32_t CHUNK = 16 * N_PRODUCERS;                  // stride between chunks
-        constexpr uint32_t SLOT = (Cfg<DT>::RAWU / 16) * CHUNK;         // one unit slot
+        constexpr uint32_t SLOT = (RawBytes<DT>::value / 16) * CHUNK; // one unit slot
+        constexpr int NSLOT = 1 + C::MAXB;
         int stage = 0;
         uint32_t phase = 0;
         for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
-            const bool diag = item.rb == item.cb;
+            const bool diag = item.cb0 == item.rb;
+            const int nB = item.ncb - (diag ? 1 : 0);          // B blocks to stage
+            const int b_first = diag ? item.cb0 + 1 : item.cb0;
             const uint8_t *unit_in = static_cast<const uint8_t *>(P.in) +
                                      (size_t)item.unit * (size_t)P.in_unit_bytes;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const bool vec = P.vec != 0;
-            const int sa = item.rb * TC_RS + sl;
-            const int sb = item.cb * TC_RS + sl;
+            int st_of[NSLOT];
+            st_of[0] = item.rb * TC_RS + sl;
+#pragma unroll
+            for (int j = 1; j < NSLOT; ++j) st_of[j] = (b_first + j - 1) * TC_RS + sl;
             auto slot_addr = [&](int k, int j) {
-                return raw_base + (uint32_t)((k % RAW) * 2 + j) * SLOT + (uint32_t)pt * 16u;
+                return raw_base + (uint32_t)((k % RAW) * NSLOT + j) * SLOT + (uint32_t)pt * 16u;
             };
             auto issue_kb = [&](int k) {
                 if (k < nkb) {
-                    issue_raw<DT>(unit_in, P.S, P.T, vec, sa, k * TC_KB_T, g, slot_addr(k, 0), CHUNK);
-                    if (!diag)
-                        issue_raw<DT>(unit_in, P.S, P.T, vec, sb, k * TC_KB_T, g, slot_addr(k, 1), CHUNK);
+#pragma unroll
+                    for (int j = 0; j < NSLOT; ++j)
+                        if (j <= nB)
+                            issue_raw<DT>(unit_in, P.S, P.T, vec, st_of[j], k * TC_KB_T, g,
+                                          slot_addr(k, j), CHUNK);
                 }
                 cp_async_commit(); // one group per K-block (empty past the end)
             };
@@ -313,17 +354,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             for (int k = 0; k < nkb; ++k) {
                 issue_kb(k + RAW - 1);
                 cp_async_wait<RAW - 1>(); // this thread's copies of K-block k have landed
-                Raw<DT> ra, rbv;
-                read_raw<DT>(slot_addr(k, 0), CHUNK, ra);
-                if (!diag) read_raw<DT>(slot_addr(k, 1), CHUNK, rbv);
+                Raw<DT> r[NSLOT];
+#pragma unroll
+                for (int j = 0; j < NSLOT; ++j)
+                    if (j <= nB) read_raw<DT>(slot_addr(k, j), CHUNK, r[j]);
                 if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
                                        p.wait_ns)) {
                     ok = false;
                     break;
                 }
-                const uint32_t st = smem_u32(tiles) + stage * STAGE_BYTES;
-                store_tile<DT>(st, sl, g, ra);
-                if (!diag) store_tile<DT>(st + TILE_BYTES, sl, g, rbv);
+                const uint32_t st = tiles_u32 + stage * STAGE;
+#pragma unroll
+                for (int j = 0; j < NSLOT; ++j)
+                    if (j <= nB) store_tile<DT>(st + j * TILE_BYTES, sl, g, r[j]);
                 fence_proxy_async_smem();
                 mbar_arrive(&bars->full[stage]);
                 if (++stage == OPS) {
@@ -348,24 +391,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const int nch = n_chunks(nkb, p.chunk_kb);
             const int s1 = item.rb * TC_RS + sl;
+            const int ngroups = 8 * item.ncb;  // groups of 8 column stations
+            const long long unit_off = (long long)item.unit * P.out_unit_elems + p1 * 2;
             for (int c = 0; c < nch; ++c, ++acc_it) {
-                const uint32_t buf = acc_it & 1, ap = (acc_it >> 1) & 1;
+                const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
                 if (!mbar_wait_bounded(&bars->acc_full[buf], ap, abort_flag, p.err, p.wait_ns)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + buf * 256 + ((uint32_t)(eq * 32) << 16);
+                const uint32_t taddr = tmem_base + buf * BUFCOLS + ((uint32_t)(eq * 32) << 16);
+                const bool last = c == nch - 1;
 #pragma unroll 1
-                for (int cc = 0; cc < 8; ++cc) {
+                for (int cc = 0; cc < ngroups; ++cc) {
                     // 16 columns = 8 column stations x 2 pols, Re and Im
                     uint32_t vre[16], vim[16];
                     tmem_ld_32x32b_x16(taddr + cc * 16, vre);
-                    tmem_ld_32x32b_x16(taddr + 128 + cc * 16, vim);
+                    tmem_ld_32x32b_x16(taddr + IMOFF + cc * 16, vim);
                     tmem_wait_ld();
-                    const int s2_0 = item.cb * TC_RS + cc * 8;
-                    const long long unit_off = (long long)item.unit * P.out_unit_elems + p1 * 2;
-                    const bool last = c == nch - 1;
+                    const int s2_0 = item.cb0 * TC_RS + cc * 8;
                     if (DT == 1) {
                         float2 *out = static_cast<float2 *>(P.out) + unit_off;
 #pragma unroll
@@ -418,30 +462,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         }
     } else {
         // ------------------------------------------------------------ MMA
-        constexpr uint32_t IDESC = idesc_f16_f32(128, 128, false);
-        constexpr uint32_t IDESC_NEG = idesc_f16_f32(128, 128, true);
+        constexpr uint32_t ID128 = idesc_f16_f32(128, 128, false);
+        constexpr uint32_t ID128N = idesc_f16_f32(128, 128, true);
+        constexpr uint32_t ID256 = idesc_f16_f32(128, 256, false);
+        constexpr uint32_t ID256N = idesc_f16_f32(128, 256, true);
         int stage = 0;
         uint32_t phase = 0;
         uint32_t acc_it = 0;
         bool ok = true;
-        const uint32_t tiles_u32 = smem_u32(tiles);
         for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
-            const bool diag = item.rb == item.cb;
+            const bool diag = item.cb0 == item.rb;
+            const bool n256 = WIDE && item.ncb == 2;
+            const uint32_t idesc = n256 ? ID256 : ID128;
+            const uint32_t idesc_neg = n256 ? ID256N : ID128N;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const int nch = n_chunks(nkb, p.chunk_kb);
             const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
             for (int c = 0; c < nch && ok; ++c, ++acc_it) {
-                const uint32_t buf = acc_it & 1, ap = (acc_it >> 1) & 1;
+                const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
                 if (!mbar_wait_bounded(&bars->acc_empty[buf], ap ^ 1, abort_flag, p.err,
                                        p.wait_ns)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_re = tmem_base + buf * 256;
-                const uint32_t d_im = d_re + 128;
+                const uint32_t d_re = tmem_base + buf * BUFCOLS;
+                const uint32_t d_im = d_re + IMOFF;
                 const int kb_lo = c * ckb;
                 const int kb_hi = min(nkb, kb_lo + ckb);
                 for (int kb = kb_lo; kb < kb_hi; ++kb) {
@@ -452,19 +500,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                     }
                     tc_fence_after();
                     if (lane == 0) {
-                        const uint32_t a = tiles_u32 + stage * STAGE_BYTES;
+                        const uint32_t a = tiles_u32 + stage * STAGE;
                         const uint32_t b = diag ? a : a + TILE_BYTES;
                         const uint32_t first = kb == kb_lo ? 1u : 0u;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks)
                             tc_mma_f16(d_re, smem_desc_sw128(a + 32 * ks),
-                                       smem_desc_sw128(b + 32 * ks), IDESC,
+                                       smem_desc_sw128(b + 32 * ks), idesc,
                                        (first && ks == 0) ? 0u : 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 64), smem_desc_sw128(b + 0), IDESC,
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 64), smem_desc_sw128(b + 0), idesc,
                                    first ? 0u : 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 96), smem_desc_sw128(b + 32), IDESC, 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 0), smem_desc_sw128(b + 64), IDESC_NEG, 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 32), smem_desc_sw128(b + 96), IDESC_NEG, 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 96), smem_desc_sw128(b + 32), idesc, 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 0), smem_desc_sw128(b + 64), idesc_neg, 1u);
+                        tc_mma_f16(d_im, smem_desc_sw128(a + 32), smem_desc_sw128(b + 96), idesc_neg, 1u);
                         tc_commit(&bars->empty[stage]);
                     }
                     __syncwarp();
@@ -493,28 +541,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     }
 }
 
-} // namespace
-
-size_t tc_smem_bytes(int dtype)
+template <int DT, bool WIDE> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
 {
-    return (size_t)(dtype == 1 ? smem_bytes<1>() : smem_bytes<2>()) + sizeof(Bars) + 1024;
+    const size_t smem = (size_t)smem_bytes<DT, WIDE>() + sizeof(Bars) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<DT, WIDE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_correlate_kernel<DT, WIDE><<<grid, TC_THREADS, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
-cudaError_t tc_launch(int dtype, const TcParams &p, int grid, cudaStream_t s)
+} // namespace
+
+cudaError_t tc_launch(int dtype, bool wide, const TcParams &p, int grid, cudaStream_t s)
 {
-    const size_t smem = tc_smem_bytes(dtype);
-    if (dtype == 1) {
-        cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<1>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_correlate_kernel<1><<<grid, TC_THREADS, smem, s>>>(p);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        tc_correlate_kernel<2><<<grid, TC_THREADS, smem, s>>>(p);
-    }
-    return cudaGetLastError();
+    if (dtype == 1) return wide ? launch_one<1, true>(p, grid, s) : launch_one<1, false>(p, grid, s);
+    return wide ? launch_one<2, true>(p, grid, s) : launch_one<2, false>(p, grid, s);
 }
 
 } // namespace corr

@@ -48,8 +48,10 @@ def check_batch(dtype, outs, hosts):
             assert rel_frobenius_per_unit(got, ref).max() < TOL_FP16
 
 
+@pytest.mark.parametrize("variant", ["narrow", "wide"])
 @pytest.mark.parametrize("dtype", ["cf16", "ci8"])
-def test_ragged_batch_one_launch(dtype):
+def test_ragged_batch_one_launch(dtype, variant, monkeypatch):
+    monkeypatch.setenv("CORR_TC_VARIANT", variant)
     from paper_1702_00844_gb300 import Plan
     plan = Plan(1, 1, 1, dtype=dtype, path="tensor")
     xs, outs, hosts = make_batch(dtype)

@@ -15,9 +15,21 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def run_tc(x: np.ndarray, S, C, T, dtype, I=1):
+VARIANTS = ["narrow", "wide"]
+
+
+@pytest.fixture(params=VARIANTS)
+def variant(request, monkeypatch):
+    """Forces the tile variant of the plans a test creates."""
+    monkeypatch.setenv("CORR_TC_VARIANT", request.param)
+    return request.param
+
+
+def run_tc(x: np.ndarray, S, C, T, dtype, I=1, expect_variant=None):
     from paper_1702_00844_gb300 import Plan
     plan = Plan(S, C, T, I, dtype=dtype, path="tensor")
+    if expect_variant:
+        assert plan.tile_variant() == expect_variant
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = plan.empty_out()
     if dtype == "ci8":
@@ -46,18 +58,18 @@ SHAPES = [(1, 1, 1), (2, 3, 2), (5, 8, 1), (64, 32, 2), (65, 33, 2), (150, 100, 
 
 
 @pytest.mark.parametrize("S,T,C", SHAPES)
-def test_int8_exact(S, T, C):
+def test_int8_exact(S, T, C, variant):
     g = synth.rng(60, S * 1000 + T)
     x8 = synth.int8_normal(g, (C, S, T, 2))
-    out = run_tc(x8, S, C, T, "ci8")
+    out = run_tc(x8, S, C, T, "ci8", expect_variant=variant)
     exact_int(out, x8)
 
 
 @pytest.mark.parametrize("S,T,C", SHAPES)
-def test_fp16_matches_oracle(S, T, C):
+def test_fp16_matches_oracle(S, T, C, variant):
     g = synth.rng(61, S * 1000 + T)
     x16 = synth.to_cf16(synth.complex_normal(g, (C, S, T, 2)))
-    got = to_numpy_vis(run_tc(x16, S, C, T, "cf16"), "cf16")
+    got = to_numpy_vis(run_tc(x16, S, C, T, "cf16", expect_variant=variant), "cf16")
     ref = oracle.correlate(x16, "cf16")
     assert np.isfinite(got).all()
     assert rel_frobenius_per_unit(got, ref).max() < TOL_FP16
@@ -65,7 +77,7 @@ def test_fp16_matches_oracle(S, T, C):
 
 
 @pytest.mark.parametrize("T", [512, 1024, 1500])
-def test_int8_adversarial_extremes_chunk_fold(T):
+def test_int8_adversarial_extremes_chunk_fold(T, variant):
     """All-(+-127) samples drive every partial sum to its bound; the 512-sample
     chunks keep each FP32 partial below 2^24 and the INT32 fold is exact."""
     S, C = 70, 1
@@ -87,6 +99,22 @@ def test_fp16_int_valued_exact_below_2pow24():
     np.testing.assert_array_equal(got, ref)
 
 
+def test_autotuner_picks_a_variant_and_variants_agree(monkeypatch):
+    """The autotuned plan reports one of the two variants, and both variants
+    give the same (exact) INT8 result on a 3-block station count."""
+    from paper_1702_00844_gb300 import Plan
+    S, T, C = 190, 96, 3
+    x8 = synth.int8_normal(synth.rng(64), (C, S, T, 2))
+    monkeypatch.delenv("CORR_TC_VARIANT", raising=False)
+    plan = Plan(S, C, T, dtype="ci8", path="tensor")
+    assert plan.tile_variant() in ("narrow", "wide")
+    outs = []
+    for v in VARIANTS:
+        monkeypatch.setenv("CORR_TC_VARIANT", v)
+        outs.append(to_numpy_int(run_tc(x8, S, C, T, "ci8", expect_variant=v)))
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_zero_samples_gives_zeros():
     from paper_1702_00844_gb300 import Plan
     for dt in ("cf16", "ci8"):
@@ -99,7 +127,8 @@ def test_zero_samples_gives_zeros():
         assert (out == 0).all()
 
 
-def test_precision_workload_full_size_sampled():
+@pytest.mark.parametrize("variant", VARIANTS, indirect=True)
+def test_precision_workload_full_size_sampled(variant):
     """The 256-station, 480-channel, 1024-sample INT8 workload in the launch
     configuration the benchmark times; sampled channels are compared with the
     oracle bit for bit (INT8) and within tolerance (FP16 of the same values),
