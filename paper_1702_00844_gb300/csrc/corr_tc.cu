@@ -261,6 +261,60 @@ __device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
     return chunk_kb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
 }
 
+// Stores the visibilities of one TMEM column group: row (s1, p1) of this
+// thread against column stations s2_0 .. s2_0+7 (both p2), masked to
+// s1 <= s2 < S. int8: converts the exact FP32 chunk sums to INT32 and adds
+// the earlier chunks' partial sums (fold).
+template <int DT>
+__device__ __forceinline__ void store_group(const TcProblem &P, long long unit_off, int s1, int s2_0,
+                                            bool fold, bool last, const uint32_t (&vre)[16],
+                                            const uint32_t (&vim)[16])
+{
+    if (DT == 1) {
+        float2 *out = static_cast<float2 *>(P.out) + unit_off;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int s2 = s2_0 + j;
+            if (s1 <= s2 && s2 < P.S) {
+                const float4 v = make_float4(__uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
+                                             __uint_as_float(vre[2 * j + 1]),
+                                             __uint_as_float(vim[2 * j + 1]));
+                st_global_cs(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4, v);
+            }
+        }
+    } else {
+        int2 *out = static_cast<int2 *>(P.out) + unit_off;
+        int4 old[8];
+        if (fold) {
+            // read every earlier partial first so the loads overlap
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int s2 = s2_0 + j;
+                old[j] = (s1 <= s2 && s2 < P.S) ? ld_global_cg(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4)
+                                                : make_int4(0, 0, 0, 0);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) old[j] = make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int s2 = s2_0 + j;
+            if (s1 <= s2 && s2 < P.S) {
+                const int4 v = make_int4(__float2int_rn(__uint_as_float(vre[2 * j])) + old[j].x,
+                                         __float2int_rn(__uint_as_float(vim[2 * j])) + old[j].y,
+                                         __float2int_rn(__uint_as_float(vre[2 * j + 1])) + old[j].z,
+                                         __float2int_rn(__uint_as_float(vim[2 * j + 1])) + old[j].w);
+                int2 *dst = out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4;
+                if (last)
+                    st_global_cs(dst, v);
+                else
+                    st_global_cg(dst, v);
+            }
+        }
+    }
+}
+
 template <int DT, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
 {
@@ -402,58 +456,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + buf * BUFCOLS + ((uint32_t)(eq * 32) << 16);
                 const bool last = c == nch - 1;
+                // Column groups of 16 TMEM columns (8 column stations x 2 pols),
+                // Re and Im; the load of the next group overlaps the stores of
+                // the current one (two register sets).
+                uint32_t ra[16], ia[16], rb2[16], ib2[16];
+                tmem_ld_32x32b_x16(taddr, ra);
+                tmem_ld_32x32b_x16(taddr + IMOFF, ia);
+                tmem_wait_ld();
 #pragma unroll 1
-                for (int cc = 0; cc < ngroups; ++cc) {
-                    // 16 columns = 8 column stations x 2 pols, Re and Im
-                    uint32_t vre[16], vim[16];
-                    tmem_ld_32x32b_x16(taddr + cc * 16, vre);
-                    tmem_ld_32x32b_x16(taddr + IMOFF + cc * 16, vim);
+                for (int cc = 0; cc < ngroups; cc += 2) {
+                    const bool has1 = cc + 1 < ngroups;
+                    if (has1) {
+                        tmem_ld_32x32b_x16(taddr + (cc + 1) * 16, rb2);
+                        tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 1) * 16, ib2);
+                    }
+                    store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
                     tmem_wait_ld();
-                    const int s2_0 = item.cb0 * TC_RS + cc * 8;
-                    if (DT == 1) {
-                        float2 *out = static_cast<float2 *>(P.out) + unit_off;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int s2 = s2_0 + j;
-                            if (s1 <= s2 && s2 < P.S) {
-                                const float4 v = make_float4(
-                                    __uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
-                                    __uint_as_float(vre[2 * j + 1]), __uint_as_float(vim[2 * j + 1]));
-                                st_global_cs(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4, v);
-                            }
+                    if (has1) {
+                        if (cc + 2 < ngroups) {
+                            tmem_ld_32x32b_x16(taddr + (cc + 2) * 16, ra);
+                            tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 2) * 16, ia);
                         }
-                    } else {
-                        int2 *out = static_cast<int2 *>(P.out) + unit_off;
-                        int4 old[8];
-                        if (c > 0) {
-                            // fold: read every earlier partial first so the loads overlap
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int s2 = s2_0 + j;
-                                old[j] = (s1 <= s2 && s2 < P.S)
-                                             ? ld_global_cg(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4)
-                                             : make_int4(0, 0, 0, 0);
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) old[j] = make_int4(0, 0, 0, 0);
-                        }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int s2 = s2_0 + j;
-                            if (s1 <= s2 && s2 < P.S) {
-                                const int4 v = make_int4(
-                                    __float2int_rn(__uint_as_float(vre[2 * j])) + old[j].x,
-                                    __float2int_rn(__uint_as_float(vim[2 * j])) + old[j].y,
-                                    __float2int_rn(__uint_as_float(vre[2 * j + 1])) + old[j].z,
-                                    __float2int_rn(__uint_as_float(vim[2 * j + 1])) + old[j].w);
-                                int2 *dst = out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4;
-                                if (last)
-                                    st_global_cs(dst, v);
-                                else
-                                    st_global_cg(dst, v);
-                            }
-                        }
+                        store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + (cc + 1) * 8, c > 0, last,
+                                        rb2, ib2);
+                        tmem_wait_ld();
                     }
                 }
                 tc_fence_before();
