@@ -69,6 +69,7 @@ typedef enum { CORR_PATH_AUTO = 0, CORR_PATH_FP32 = 1, CORR_PATH_TENSOR = 2 } co
 /* Plan flags. */
 #define CORR_FLAG_GAINS 0x1u      /* allocate the gain-calibration workspace */
 #define CORR_FLAG_NO_AUTOTUNE 0x2u /* skip timed tile selection at create */
+#define CORR_FLAG_HOST_IO 0x4u     /* allocate staging for corr_correlate_host */
 
 typedef struct {
     int n_stations;     /* S >= 1                                   (Section 2) */
@@ -106,6 +107,18 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out);
  * fully overwritten. d_in may be NULL when n_samples is 0 (the output is
  * then all zeros). Asynchronous on stream; capturable in a CUDA graph. */
 corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream);
+
+/* corr_correlate with HOST buffers (h_in, h_out: same layouts as above, in
+ * host memory; page-locked memory gives overlapped copies). The channels
+ * are streamed in chunks of about 64 MiB of input: the host-to-device copy
+ * of chunk i+1 and the device-to-host copy of chunk i-1 overlap the kernel
+ * of chunk i (two plan-owned staging buffers, two plan-owned copy streams).
+ * This is the overlap of transfers and correlation that Section 3.6 and
+ * Section 4.4 identify as the bound of a correlator fed over a host link.
+ * Requires a plan created with CORR_FLAG_HOST_IO. Asynchronous: everything
+ * is ordered before later work on stream, so synchronizing stream covers the
+ * whole call. The host buffers must stay valid until then. */
+corr_status_t corr_correlate_host(corr_handle_t h, const void *h_in, void *h_out, void *stream);
 
 /* Correlates a ragged batch of n_sub independent sub-arrays (each with its
  * own S, C and T, channels independent as in Section 2) in one persistent

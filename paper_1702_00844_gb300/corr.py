@@ -17,6 +17,7 @@ DTYPES = {"cf32": 0, "cf16": 1, "ci8": 2}
 PATHS = {"auto": 0, "fp32": 1, "tensor": 2}
 FLAG_GAINS = 0x1
 FLAG_NO_AUTOTUNE = 0x2
+FLAG_HOST_IO = 0x4
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory",
           4: "CUDA error", 5: "timeout"}
 
@@ -57,6 +58,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_create.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
     L.corr_correlate.argtypes = [vp, vp, vp, vp]
     L.corr_correlate_batched.argtypes = [vp, ip, ctypes.POINTER(Subarray), vp]
+    L.corr_correlate_host.argtypes = [vp, vp, vp, vp]
     L.corr_gain_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.corr_gain_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.corr_destroy.argtypes = [vp]
@@ -77,7 +79,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_gain_backward_noalloc.restype = ip
     L.corr_noalloc_scratch_bytes.argtypes = []
     L.corr_noalloc_scratch_bytes.restype = ctypes.c_size_t
-    for name in ("corr_create", "corr_correlate", "corr_correlate_batched", "corr_gain_loss",
+    for name in ("corr_create", "corr_correlate", "corr_correlate_host", "corr_correlate_batched", "corr_gain_loss",
                  "corr_gain_backward", "corr_destroy", "corr_get_error"):
         getattr(L, name).restype = ip
     _LIB = L
@@ -155,6 +157,19 @@ class Plan:
             raise ValueError(f"samples: expected {want} elements of {torch_dtype(self.dtype)}")
         _check(self.L.corr_correlate(self.h, _ptr(x), _ptr(out), _stream_handle(stream)),
                "corr_correlate")
+        return out
+
+    def correlate_host(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+        """``corr_correlate_host``: ``x`` and ``out`` are CPU tensors (pin them
+        for overlapped copies). Returns ``out``; synchronize the stream before
+        reading it."""
+        if out is None:
+            out = self.empty_out("cpu")
+        if x.is_cuda or out.is_cuda or not x.is_contiguous() or not out.is_contiguous():
+            raise ValueError("contiguous host tensors expected")
+        _check(self.L.corr_correlate_host(self.h, ctypes.c_void_p(x.data_ptr() or None),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "corr_correlate_host")
         return out
 
     def correlate_batched(self, pairs: Sequence[Tuple[torch.Tensor, torch.Tensor]],

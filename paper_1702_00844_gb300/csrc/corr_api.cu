@@ -42,6 +42,12 @@ struct corr_plan {
     int4 *d_bitems = nullptr;
     int n_bitems = 0;
     int b_variant = TC_NARROW;
+    // host-buffer streaming (CORR_FLAG_HOST_IO)
+    int chunk_units = 0;
+    void *d_stage_in[2] = {nullptr, nullptr};
+    void *d_stage_out[2] = {nullptr, nullptr};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
     // gain calibration
     float2 *d_R = nullptr;     // recomputed raw visibilities
     float2 *d_W = nullptr;     // W' per channel
@@ -166,10 +172,10 @@ corr_status_t cuda_status(cudaError_t e)
     return CORR_ERR_CUDA;
 }
 
-corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
+corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long long units,
+                           cudaStream_t s)
 {
     const corr_desc_t &d = h->d;
-    const long long units = (long long)d.n_channels * d.n_integrations;
     const size_t out_bytes = (size_t)(units * n_baselines(d.n_stations) * 4 * 8);
     if (d.n_samples == 0) return cuda_status(cudaMemsetAsync(d_out, 0, out_bytes, s));
     if (h->path == CORR_PATH_FP32) {
@@ -177,6 +183,7 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
         corr_status_t st = encode_fp32_map(&m, d_in, d.n_stations, d.n_samples, (int)units, h->fp.tc);
         if (st != CORR_OK) return st;
         Fp32Params p = h->fp;
+        p.n_units = (int)units;
         p.out = static_cast<float2 *>(d_out);
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
@@ -185,13 +192,26 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
     TcParams p{};
     p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype);
     p.probs = nullptr;
-    p.items = h->d_items;
-    p.n_items = h->n_items;
+    p.items = h->d_items; // unit-major, so the first units' items are a prefix
+    p.n_items = (int)((long long)h->n_items / ((long long)d.n_channels * d.n_integrations) * units);
     p.chunk_kb = d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return cuda_status(tc_launch(d.dtype, h->tc_variant == TC_WIDE, p, h->tc_grid, s));
+    return cuda_status(tc_launch(d.dtype, h->tc_variant == TC_WIDE, p,
+                                 std::max(1, std::min(p.n_items, h->sm_count)), s));
 }
+
+corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
+{
+    return launch_units(h, d_in, d_out, (long long)h->d.n_channels * h->d.n_integrations, s);
+}
+
+size_t in_unit_bytes(const corr_desc_t &d)
+{
+    return (size_t)d.n_stations * d.n_samples * bytes_per_sample(d.dtype);
+}
+
+size_t out_unit_bytes(const corr_desc_t &d) { return (size_t)n_baselines(d.n_stations) * 4 * 8; }
 
 // ------------------------------------------------------------------ autotuner
 // The tile variant of the tensor path is chosen per (device, dtype, S, T) by
@@ -422,6 +442,25 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
                 break;
             h->tc_grid = std::max(1, std::min(h->n_items, h->sm_count));
         }
+        if (d.flags & CORR_FLAG_HOST_IO) {
+            // chunks of about 64 MiB of input (at least one channel)
+            const size_t ub = std::max<size_t>(1, in_unit_bytes(d));
+            h->chunk_units = (int)std::max<long long>(
+                1, std::min<long long>(units, (long long)((64ull << 20) / ub)));
+            const size_t ib = (size_t)h->chunk_units * in_unit_bytes(d);
+            const size_t ob = (size_t)h->chunk_units * out_unit_bytes(d);
+            for (int b = 0; b < 2 && st == CORR_OK; ++b) {
+                st = cuda_status(cudaMalloc(&h->d_stage_in[b], std::max<size_t>(ib, 16)));
+                if (st == CORR_OK) st = cuda_status(cudaMalloc(&h->d_stage_out[b], ob));
+                if (st == CORR_OK) st = cuda_status(cudaEventCreateWithFlags(&h->ev_in[b], cudaEventDisableTiming));
+                if (st == CORR_OK) st = cuda_status(cudaEventCreateWithFlags(&h->ev_comp[b], cudaEventDisableTiming));
+                if (st == CORR_OK) st = cuda_status(cudaEventCreateWithFlags(&h->ev_out[b], cudaEventDisableTiming));
+            }
+            if (st == CORR_OK) st = cuda_status(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
+            if (st == CORR_OK) st = cuda_status(cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
+            if (st == CORR_OK) st = cuda_status(cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
+            if (st != CORR_OK) break;
+        }
         if (d.flags & CORR_FLAG_GAINS) {
             const long long S = d.n_stations, N = 2 * S;
             if ((st = cuda_status(cudaMalloc(&h->d_R, (size_t)(units * n_baselines(S) * 4 * 8)))) != CORR_OK) break;
@@ -442,6 +481,48 @@ corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, voi
     if (!h || !d_out || !aligned16(d_out)) return CORR_ERR_INVALID_ARG;
     if (h->d.n_samples > 0 && (!d_in || !aligned16(d_in))) return CORR_ERR_INVALID_ARG;
     return launch_correlate(h, d_in, d_out, static_cast<cudaStream_t>(stream));
+}
+
+corr_status_t corr_correlate_host(corr_handle_t h, const void *h_in, void *h_out, void *stream)
+{
+    if (!h || !h_out || !(h->d.flags & CORR_FLAG_HOST_IO)) return CORR_ERR_INVALID_ARG;
+    const corr_desc_t &d = h->d;
+    if (d.n_samples > 0 && !h_in) return CORR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long units = (long long)d.n_channels * d.n_integrations;
+    const long long cu = h->chunk_units;
+    const long long nch = (units + cu - 1) / cu;
+    const size_t ib = in_unit_bytes(d), ob = out_unit_bytes(d);
+    corr_status_t st = cuda_status(cudaEventRecord(h->ev_start, s));
+    if (st == CORR_OK) st = cuda_status(cudaStreamWaitEvent(h->s_h2d, h->ev_start, 0));
+    if (st == CORR_OK) st = cuda_status(cudaStreamWaitEvent(h->s_d2h, h->ev_start, 0));
+    for (long long i = 0; i < nch && st == CORR_OK; ++i) {
+        const int b = (int)(i & 1);
+        const long long u0 = i * cu;
+        const long long nu = std::min(cu, units - u0);
+        // staging buffer b was last read by the kernel of chunk i-2 and its
+        // output last copied out by the D2H of chunk i-2
+        if (i >= 2) st = cuda_status(cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0));
+        if (st == CORR_OK && ib * nu > 0)
+            st = cuda_status(cudaMemcpyAsync(h->d_stage_in[b],
+                                             static_cast<const char *>(h_in) + (size_t)u0 * ib,
+                                             (size_t)nu * ib, cudaMemcpyHostToDevice, h->s_h2d));
+        if (st == CORR_OK) st = cuda_status(cudaEventRecord(h->ev_in[b], h->s_h2d));
+        if (st == CORR_OK) st = cuda_status(cudaStreamWaitEvent(s, h->ev_in[b], 0));
+        if (st == CORR_OK && i >= 2) st = cuda_status(cudaStreamWaitEvent(s, h->ev_out[b], 0));
+        if (st == CORR_OK) st = launch_units(h, h->d_stage_in[b], h->d_stage_out[b], nu, s);
+        if (st == CORR_OK) st = cuda_status(cudaEventRecord(h->ev_comp[b], s));
+        if (st == CORR_OK) st = cuda_status(cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0));
+        if (st == CORR_OK)
+            st = cuda_status(cudaMemcpyAsync(static_cast<char *>(h_out) + (size_t)u0 * ob,
+                                             h->d_stage_out[b], (size_t)nu * ob,
+                                             cudaMemcpyDeviceToHost, h->s_d2h));
+        if (st == CORR_OK) st = cuda_status(cudaEventRecord(h->ev_out[b], h->s_d2h));
+    }
+    // the caller's stream completes only after every copy back
+    for (int b = 0; b < 2 && st == CORR_OK && b < nch; ++b)
+        st = cuda_status(cudaStreamWaitEvent(s, h->ev_out[b], 0));
+    return st;
 }
 
 corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_subarray_t *subs,
@@ -603,6 +684,16 @@ corr_status_t corr_destroy(corr_handle_t h)
     cudaFree(h->d_items);
     cudaFree(h->d_bprobs);
     cudaFree(h->d_bitems);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->d_stage_in[b]);
+        cudaFree(h->d_stage_out[b]);
+        if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
+        if (h->ev_comp[b]) cudaEventDestroy(h->ev_comp[b]);
+        if (h->ev_out[b]) cudaEventDestroy(h->ev_out[b]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+    if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     cudaFree(h->d_R);
     cudaFree(h->d_W);
     cudaFree(h->d_partial);
