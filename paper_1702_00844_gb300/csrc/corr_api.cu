@@ -36,6 +36,11 @@ struct corr_plan {
     int tc_grid = 0;
     int tc_variant = TC_NARROW;
     float tune_ms[2] = {0.f, 0.f};
+    // int8 power check / redo list (single problem and batches)
+    int *d_redo_mark = nullptr;
+    int4 *d_redo_items = nullptr;
+    int *d_redo_count = nullptr;
+    int redo_cap = 0;
     // ragged batches
     std::vector<corr_subarray_t> batch_key;
     TcProblem *d_bprobs = nullptr;
@@ -172,6 +177,55 @@ corr_status_t cuda_status(cudaError_t e)
     return CORR_ERR_CUDA;
 }
 
+// Grows the redo buffers to hold n items (allocation: create time or the
+// first batched call with a new set, never during a capturable call).
+corr_status_t ensure_redo(corr_plan *h, int n)
+{
+    if (n <= h->redo_cap) return CORR_OK;
+    cudaFree(h->d_redo_mark);
+    cudaFree(h->d_redo_items);
+    h->d_redo_mark = nullptr;
+    h->d_redo_items = nullptr;
+    h->redo_cap = 0;
+    corr_status_t st;
+    if (!h->d_redo_count && (st = cuda_status(cudaMalloc(&h->d_redo_count, sizeof(int)))) != CORR_OK) return st;
+    if ((st = cuda_status(cudaMalloc(&h->d_redo_mark, (size_t)n * sizeof(int)))) != CORR_OK) return st;
+    if ((st = cuda_status(cudaMalloc(&h->d_redo_items, (size_t)n * sizeof(int4)))) != CORR_OK) return st;
+    h->redo_cap = n;
+    return CORR_OK;
+}
+
+// Launches the tensor kernel for p.items[0 .. p.n_items). int8 with more than
+// one 512-sample chunk runs unchunked with the station power check, then a
+// chunked launch over the items the check rejected (usually none).
+corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, bool wide, int max_T, cudaStream_t s)
+{
+    const int grid = std::max(1, std::min(p.n_items, h->sm_count));
+    const bool checked = dtype == CORR_CI8 && max_T > TC_INT8_CHUNK_KB * TC_KB_T && h->redo_cap >= p.n_items;
+    if (!checked) {
+        p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
+        return cuda_status(tc_launch(dtype, wide, p, grid, s));
+    }
+    corr_status_t st = cuda_status(cudaMemsetAsync(h->d_redo_mark, 0, (size_t)p.n_items * sizeof(int), s));
+    if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count, 0, sizeof(int), s));
+    if (st != CORR_OK) return st;
+    TcParams a = p;
+    a.chunk_kb = 0;
+    a.check_power = 1;
+    a.redo_mark = h->d_redo_mark;
+    a.redo_items = h->d_redo_items;
+    a.redo_count = h->d_redo_count;
+    st = cuda_status(tc_launch(dtype, wide, a, grid, s));
+    if (st != CORR_OK) return st;
+    TcParams b = p;
+    b.items = h->d_redo_items;
+    b.n_items = p.n_items;          // upper bound; the count is read on the device
+    b.n_items_dev = h->d_redo_count;
+    b.chunk_kb = TC_INT8_CHUNK_KB;
+    b.check_power = 0;
+    return cuda_status(tc_launch(dtype, wide, b, h->sm_count, s));
+}
+
 corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long long units,
                            cudaStream_t s)
 {
@@ -194,11 +248,9 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     p.probs = nullptr;
     p.items = h->d_items; // unit-major, so the first units' items are a prefix
     p.n_items = (int)((long long)h->n_items / ((long long)d.n_channels * d.n_integrations) * units);
-    p.chunk_kb = d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return cuda_status(tc_launch(d.dtype, h->tc_variant == TC_WIDE, p,
-                                 std::max(1, std::min(p.n_items, h->sm_count)), s));
+    return run_tensor(h, p, d.dtype, h->tc_variant == TC_WIDE, d.n_samples, s);
 }
 
 corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
@@ -254,18 +306,17 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
         p.prob0 = make_problem(d_in, d_out, S, T, units, h->d.dtype);
         p.items = d_items;
         p.n_items = (int)items.size();
-        p.chunk_kb = h->d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
-        const int grid = std::max(1, std::min(p.n_items, h->sm_count));
+        if (h->d.dtype == CORR_CI8 && (st = ensure_redo(h, p.n_items)) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
         for (int i = 0; i < 2 && st == CORR_OK; ++i)
-            st = cuda_status(tc_launch(h->d.dtype, variant == TC_WIDE, p, grid, 0));
+            st = run_tensor(h, p, h->d.dtype, variant == TC_WIDE, T, 0);
         if (st != CORR_OK) break;
         cudaEventRecord(e0, 0);
         for (int i = 0; i < 3 && st == CORR_OK; ++i)
-            st = cuda_status(tc_launch(h->d.dtype, variant == TC_WIDE, p, grid, 0));
+            st = run_tensor(h, p, h->d.dtype, variant == TC_WIDE, T, 0);
         cudaEventRecord(e1, 0);
         if (st != CORR_OK) break;
         if ((st = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
@@ -441,6 +492,7 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
                                              cudaMemcpyHostToDevice))) != CORR_OK)
                 break;
             h->tc_grid = std::max(1, std::min(h->n_items, h->sm_count));
+            if (d.dtype == CORR_CI8 && (st = ensure_redo(h, h->n_items)) != CORR_OK) break;
         }
         if (d.flags & CORR_FLAG_HOST_IO) {
             // chunks of about 64 MiB of input (at least one channel)
@@ -590,6 +642,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                 return e;
         }
         h->n_bitems = (int)items.size();
+        if (h->d.dtype == CORR_CI8 && (e = ensure_redo(h, h->n_bitems)) != CORR_OK) return e;
         h->batch_key.assign(subs, subs + n_sub);
     }
     for (int i = 0; i < n_sub; ++i)
@@ -603,11 +656,11 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     p.probs = h->d_bprobs;
     p.items = h->d_bitems;
     p.n_items = h->n_bitems;
-    p.chunk_kb = h->d.dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    const int grid = std::max(1, std::min(h->n_bitems, h->sm_count));
-    return cuda_status(tc_launch(h->d.dtype, h->b_variant == TC_WIDE, p, grid, st));
+    int max_T = 0;
+    for (int i = 0; i < n_sub; ++i) max_T = std::max(max_T, subs[i].n_samples);
+    return run_tensor(h, p, h->d.dtype, h->b_variant == TC_WIDE, max_T, st);
 }
 
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
@@ -682,6 +735,9 @@ corr_status_t corr_destroy(corr_handle_t h)
     cudaDeviceSynchronize();
     cudaFree(h->d_err);
     cudaFree(h->d_items);
+    cudaFree(h->d_redo_mark);
+    cudaFree(h->d_redo_items);
+    cudaFree(h->d_redo_count);
     cudaFree(h->d_bprobs);
     cudaFree(h->d_bitems);
     for (int b = 0; b < 2; ++b) {

@@ -19,9 +19,18 @@ struct TcProblem {
 struct TcParams {
     TcProblem prob0;          // used when probs == nullptr
     const TcProblem *probs;   // device array (ragged batches)
-    const int4 *items;        // {problem, unit, row block, col block}
+    const int4 *items;        // {problem, unit, row block, col block | n blocks << 16}
     int n_items;
+    const int *n_items_dev;   // if set, the item count is read from device memory
     int chunk_kb;             // K-blocks per exact accumulation chunk (0 = all)
+    // int8 without chunks: producers bound every partial sum of a tile by the
+    // largest station power sum_t |x|^2 of its stations (Cauchy-Schwarz); a
+    // tile whose bound exceeds 2^24 is appended once to the redo list, which
+    // a second, chunked launch recomputes (overwriting its output).
+    int check_power;
+    int *redo_mark;           // per item: 0, or 1 once appended (zeroed per call)
+    int4 *redo_items;
+    int *redo_count;
     int *err;                 // device error word
     unsigned long long wait_ns;
 };

@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
+    const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
 
     if (tid == 0) {
         for (int s = 0; s < OPS; ++s) {
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         constexpr int NSLOT = 1 + C::MAXB;
         int stage = 0;
         uint32_t phase = 0;
-        for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const bool diag = item.cb0 == item.rb;
@@ -384,6 +385,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                                      (size_t)item.unit * (size_t)P.in_unit_bytes;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const bool vec = P.vec != 0;
+            const bool check = DT == 2 && p.check_power != 0;
+            int power[NSLOT];   // this thread's share of sum_t |x|^2 per staged station
+#pragma unroll
+            for (int j = 0; j < NSLOT; ++j) power[j] = 0;
             int st_of[NSLOT];
             st_of[0] = item.rb * TC_RS + sl;
 #pragma unroll
@@ -421,6 +426,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
 #pragma unroll
                 for (int j = 0; j < NSLOT; ++j)
                     if (j <= nB) store_tile<DT>(st + j * TILE_BYTES, sl, g, r[j]);
+                if (check) {
+#pragma unroll
+                    for (int j = 0; j < NSLOT; ++j)
+                        if (j <= nB)
+#pragma unroll
+                            for (int q = 0; q < (int)(sizeof(Raw<DT>) / 16); ++q) {
+                                // 4 int8 (re, im of both pols) per word: sum of squares
+                                power[j] = __dp4a((int)r[j].v[q].x, (int)r[j].v[q].x, power[j]);
+                                power[j] = __dp4a((int)r[j].v[q].y, (int)r[j].v[q].y, power[j]);
+                                power[j] = __dp4a((int)r[j].v[q].z, (int)r[j].v[q].z, power[j]);
+                                power[j] = __dp4a((int)r[j].v[q].w, (int)r[j].v[q].w, power[j]);
+                            }
+                }
                 fence_proxy_async_smem();
                 mbar_arrive(&bars->full[stage]);
                 if (++stage == OPS) {
@@ -430,6 +448,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             }
             cp_async_wait<0>();
             if (!ok) break;
+            if (check) {
+                // station power = sum over the 4 threads of the station (both
+                // pols together, which bounds each pol); any station above
+                // 2^24 makes the unchunked FP32 sums of this tile unproven.
+                bool unsafe = false;
+#pragma unroll
+                for (int j = 0; j < NSLOT; ++j) {
+                    int v = min(power[j], 1 << 25); // clamp: keeps the test, avoids overflow
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    unsafe |= j <= nB && v > (1 << 24);
+                }
+                if (__any_sync(0xffffffffu, unsafe) && lane == 0) {
+                    if (atomicExch(p.redo_mark + it, 1) == 0) {
+                        const int slot = atomicAdd(p.redo_count, 1);
+                        p.redo_items[slot] = __ldg(p.items + it);
+                    }
+                }
+            }
         }
     } else if (warp < WARP_MMA) {
         // ------------------------------------------------------- epilogue
@@ -439,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         const int p1 = row & 1;
         uint32_t acc_it = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
@@ -496,7 +533,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         uint32_t phase = 0;
         uint32_t acc_it = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const bool diag = item.cb0 == item.rb;
