@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["precision", "precision-f16", "production"],
+                    default="precision",
+                    help="precision: int8 tensor path at 256 stations (the headline); "
+                         "precision-f16: the same samples on the f16 tensor path; "
+                         "production: the 64-station FP32 workload on the FP32 path")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/FP32/batch/adjoint side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -308,13 +313,36 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
 
+    wl = args.workload
     x8 = synth.precision_device(C3, S3, T3, "cuda", rank=rank)
-    plan = Plan(S3, C3, T3, dtype="ci8", path="tensor")
+    if wl == "production":
+        S, C, T, I = 64, 256, 768, 10
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(synth.BASE_SEED + 2 + 7919 * rank)
+        x = torch.randn((I, C, S, T, 2), dtype=torch.complex64, device="cuda", generator=gen)
+        plan = Plan(S, C, T, I, dtype="cf32", path="fp32")
+        units, dtype_label = C * I, "f32"
+        workload = ("production: 64 stations, 2 pols, 256 channels, 768 samples, 10 integrations, "
+                    "complex64 N(0,1), FP32 CUDA-core path")
+    else:
+        S, C, T, I = S3, C3, T3, 1
+        if wl == "precision-f16":
+            x = x8.to(torch.float16)
+            plan = Plan(S, C, T, dtype="cf16", path="tensor")
+            dtype_label = "f16"
+            workload = WORKLOAD.replace("INT32 visibilities (bit-exact)",
+                                        "cast to f16, FP32 accumulation")
+        else:
+            x = x8
+            plan = Plan(S, C, T, dtype="ci8", path="tensor")
+            dtype_label = "s8"
+            workload = WORKLOAD
+        units = C
     out = plan.empty_out()
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.correlate(x8, out)
+        plan.correlate(x, out)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -337,15 +365,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     plan.check_error()
     ms_step = ms_total / args.steps
-    ops = ops_of(S3, T3, C3)
+    ops = ops_of(S, T, units)
     value = ops * world * args.steps / (ms_total * 1e-3) / 1e12
 
     # end to end through the public API with host buffers: corr_correlate_host
     # streams the step's samples from page-locked memory in chunks, with the
     # copies overlapping the kernels, and copies the visibilities back.
     from paper_1702_00844_gb300 import FLAG_HOST_IO
-    plan_io = Plan(S3, C3, T3, dtype="ci8", path="tensor", flags=FLAG_HOST_IO)
-    xh = x8.cpu().pin_memory()
+    plan_io = Plan(S, C, T, I, dtype=plan.dtype, path="fp32" if wl == "production" else "tensor",
+                   flags=FLAG_HOST_IO)
+    xh = x.cpu().pin_memory()
     oh = plan_io.empty_out("cpu").pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
     e2e_ms = time_launches(lambda: plan_io.correlate_host(xh, oh), e2e_steps, 1, stream)
@@ -358,31 +387,51 @@ def run_ours(args):
     del xh, oh, plan_io
 
     peaks, peak_src = measured_peaks()
-    peak = float(peaks.get("bf16_tflops", 1900.0))
+    in_bps = {"s8": 4, "f16": 8, "f32": 16}[dtype_label]
+    alg_bytes = units * (S * T * in_bps + S * (S + 1) // 2 * 32)
     achieved = ops / (ms_step * 1e-3) / 1e12
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(),
-            "kernel": "tc_correlate_kernel<int8>",
-            "peak_source": f"{peak_src} bf16 dense burst (f16 dense runs at the bf16 rate)",
-            "algorithmic_bytes": C3 * (S3 * T3 * 4 + S3 * (S3 + 1) // 2 * 32),
-            "hbm_bound_TOPS": ops / (C3 * (S3 * T3 * 4 + S3 * (S3 + 1) // 2 * 32)
-                                     / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)) / 1e12}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if wl == "production":
+        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x maximum SM clock
+        peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "fp32_correlate_kernel",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"}
+    else:
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic() if wl == "precision" else None,
+                "kernel": f"tc_correlate_kernel<{dtype_label}, {plan.tile_variant()}>",
+                "peak_source": f"{peak_src} bf16 dense burst (f16 dense runs at the bf16 rate)"}
+    roof["algorithmic_bytes"] = alg_bytes
+    roof["hbm_bound_TOPS"] = ops / (alg_bytes / (hbm * 1e9)) / 1e12
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "s8",
-            "data": "synthetic (seeded device Philox, same recipe as the precision workload)",
-            "config": {"workload": WORKLOAD, "stations": S3, "pols": 2, "channels": C3,
-                       "samples": T3, "path": "tcgen05 kind::f16 with exact int8->f16 widening, "
-                       "512-sample chunks folded to INT32",
-                       "l2": "inputs 503 MB and outputs 505 MB exceed L2 (129 MB): no flush",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_label,
+            "data": "synthetic (seeded device Philox, same recipe as the workload)",
+            "config": {"workload": workload, "stations": S, "pols": 2, "channels": C,
+                       "integrations": I, "samples": T,
+                       "path": {"s8": "tcgen05 kind::f16 with exact int8->f16 widening; exact "
+                                      "FP32 sums by a station-power bound, chunked INT32 fold "
+                                      "for tiles that fail it",
+                                "f16": "tcgen05 kind::f16, FP32 accumulation in TMEM",
+                                "f32": "FP32 CUDA cores, TMA-staged samples"}[dtype_label],
+                       "l2": f"inputs {units * S * T * in_bps / 1e6:.0f} MB and outputs "
+                             f"{units * S * (S + 1) // 2 * 32 / 1e6:.0f} MB; inputs exceed L2 "
+                             "(129 MB): no flush",
                        "parallelism": f"channels per GPU fixed, {world} GPU(s), no collective"},
-            "clocks": clk.summary(), "e2e": e2e, "roofline": roof, "gpu_launches": args.steps}
-    if rank == 0 and world == 1 and not args.no_secondary:
+            "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+            # one tensor launch per step, plus the (usually empty) redo launch
+            # of the int8 path when T exceeds one 512-sample chunk
+            "gpu_launches": args.steps * (2 if dtype_label == "s8" and T > 512 else 1)}
+    if rank == 0 and world == 1 and not args.no_secondary and wl == "precision":
         line["paths"] = secondary(x8, torch)
         fp32 = line["paths"]["fp32_cuda_core_precision"]["TOPS"]
         line["paths"]["tensor_int8_vs_fp32_same_samples"] = value / fp32
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and wl == "precision":
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
