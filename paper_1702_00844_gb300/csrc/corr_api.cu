@@ -119,7 +119,8 @@ void fp32_config(corr_plan *h)
     p.n_units = h->d.n_channels * h->d.n_integrations;
     p.nq = (S + 3) / 4;
     p.nsub = p.nq * (p.nq + 1) / 2;
-    p.groups = (p.nsub + 255) / 256;
+    // at most 192 threads per CTA: two CTAs of 168-register threads fit an SM
+    p.groups = (p.nsub + 191) / 192;
     p.group_size = (p.nsub + p.groups - 1) / p.groups;
     h->fp_threads = ((p.group_size + 31) / 32) * 32;
     const int nbox = (S + 7) / 8;

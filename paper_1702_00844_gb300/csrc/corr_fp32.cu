@@ -10,6 +10,9 @@
 // assigned to neighbouring threads so they consume the same samples at the
 // same time (Section 2's inter-tile reuse through co-scheduling).
 //
+// Registers are capped at 168 per thread and CTAs at 192 threads so that two
+// CTAs share an SM (at most 3 warps per SM sub-partition).
+//
 // Samples are staged by TMA: each stage holds `tc` samples of every station
 // the CTA needs, as boxes of 8 stations stored time-major
 // ([box][t][8 stations][2 pols x complex]). Thread j reads its four column
@@ -36,7 +39,7 @@ __device__ __forceinline__ void decode_subtile(int nq, int k, int &i, int &j)
     j = row + (k - off);
 }
 
-__global__ void __launch_bounds__(256) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const Fp32Params p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) fp32_correlate_kernel(const __grid_consta
         if (ok) {
             const float4 *base = sm4 + (size_t)st * stage_f4;
             const int tn = min(p.tc, p.T - kc * p.tc);
-#pragma unroll 2
+#pragma unroll 1
             for (int t = 0; t < tn; ++t) {
                 float4 r[4], c[4];
 #pragma unroll
