@@ -39,6 +39,16 @@ __device__ __forceinline__ void decode_subtile(int nq, int k, int &i, int &j)
     j = row + (k - off);
 }
 
+// Waits for the TMA loads of chunks kc .. kc + STAGES - 1 (those issued by
+// the time chunk kc is consumed) to land; fixed 2 s bound per stage. Called
+// only when the kernel gives up, before the CTA exits.
+__device__ __noinline__ void drain_issued(uint64_t *full, int kc, int nchunks, int *err)
+{
+    int dummy = 0;
+    for (int c = kc; c < min(nchunks, kc + FP32_STAGES); ++c)
+        mbar_wait_bounded(&full[c % FP32_STAGES], (c / FP32_STAGES) & 1, &dummy, err, 2000000000ull);
+}
+
 __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const Fp32Params p)
 {
@@ -133,7 +143,12 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
             }
         }
         __syncthreads();
-        if (abort_flag) break;
+        if (abort_flag) {
+            // Let every issued TMA load land before the CTA (and its shared
+            // memory) goes away; fixed 2 s bound per stage.
+            if (tid == 0) drain_issued(full, kc, nchunks, p.err);
+            break;
+        }
         if (tid == 0 && kc + FP32_STAGES < nchunks) issue(kc + FP32_STAGES);
     }
 

@@ -589,11 +589,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                 __syncwarp();
             }
         }
-        // Wait (bounded) for every MMA this thread issued before TMEM is freed.
+        // Wait for every MMA this thread issued before TMEM is freed. This wait
+        // keeps a fixed 2 s bound whatever p.wait_ns is, so that an aborted
+        // kernel never frees TMEM under a running MMA.
         if (lane == 0) tc_commit(&bars->fin);
         __syncwarp();
         int dummy_abort = 0;
-        mbar_wait_bounded(&bars->fin, 0, &dummy_abort, p.err, p.wait_ns);
+        mbar_wait_bounded(&bars->fin, 0, &dummy_abort, p.err, 2000000000ull);
     }
 
     tc_fence_before();
