@@ -110,7 +110,7 @@ corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, voi
 
 /* corr_correlate with HOST buffers (h_in, h_out: same layouts as above, in
  * host memory; page-locked memory gives overlapped copies). The channels
- * are streamed in chunks of about 64 MiB of input: the host-to-device copy
+ * are streamed in chunks of about 32 MiB of input: the host-to-device copy
  * of chunk i+1 and the device-to-host copy of chunk i-1 overlap the kernel
  * of chunk i (two plan-owned staging buffers, two plan-owned copy streams).
  * This is the overlap of transfers and correlation that Section 3.6 and

@@ -496,10 +496,13 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             if (d.dtype == CORR_CI8 && (st = ensure_redo(h, h->n_items)) != CORR_OK) break;
         }
         if (d.flags & CORR_FLAG_HOST_IO) {
-            // chunks of about 64 MiB of input (at least one channel)
+            // chunks of about 32 MiB of input (CORR_HOST_CHUNK_MB overrides;
+            // at least one channel)
+            size_t chunk_mb = 32;
+            if (const char *e = std::getenv("CORR_HOST_CHUNK_MB")) chunk_mb = std::max(1ul, std::strtoul(e, nullptr, 10));
             const size_t ub = std::max<size_t>(1, in_unit_bytes(d));
             h->chunk_units = (int)std::max<long long>(
-                1, std::min<long long>(units, (long long)((64ull << 20) / ub)));
+                1, std::min<long long>(units, (long long)((chunk_mb << 20) / ub)));
             const size_t ib = (size_t)h->chunk_units * in_unit_bytes(d);
             const size_t ob = (size_t)h->chunk_units * out_unit_bytes(d);
             for (int b = 0; b < 2 && st == CORR_OK; ++b) {

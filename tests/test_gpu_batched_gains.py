@@ -185,3 +185,33 @@ def test_differentiation_workload_full_size():
         gx = grad_x[c].cpu().numpy().astype(np.complex128)[None]
         assert np.abs(gg - gref).max() < 1e-4 * np.abs(gref).max()
         assert np.abs(gx - xref).max() < 1e-4 * np.abs(xref).max()
+
+
+def test_ragged_int8_batch_with_extreme_subarray_takes_redo_path(monkeypatch):
+    """One sub-array of all +-127 samples (station power above 2^24) in a
+    batch with T > 512: its tiles fail the power check and are recomputed in
+    exact 512-sample chunks, the others are accepted unchunked; all exact."""
+    from paper_1702_00844_gb300 import Plan
+    shapes = [(70, 2, 1024), (130, 1, 640), (33, 3, 1500)]
+    xs, outs, hosts = [], [], []
+    for k, (S, C, T) in enumerate(shapes):
+        g = synth.rng(71, k)
+        if k == 2:
+            h = np.where(g.random((C, S, T, 2, 2)) < 0.5, -127, 127).astype(np.int8)
+        else:
+            h = synth.int8_normal(g, (C, S, T, 2))
+        hosts.append(h)
+        xs.append(torch.from_numpy(h).cuda())
+        outs.append(torch.full((C, S * (S + 1) // 2, 2, 2, 2), 0x7FFFFFFF, dtype=torch.int32,
+                               device="cuda"))
+    for variant in ("narrow", "wide"):
+        monkeypatch.setenv("CORR_TC_VARIANT", variant)
+        plan = Plan(1, 1, 1, dtype="ci8", path="tensor")
+        plan.correlate_batched(list(zip(xs, outs)), shapes)
+        torch.cuda.synchronize()
+        plan.check_error()
+        for (S, C, T), o, h in zip(shapes, outs, hosts):
+            ref = oracle.correlate(h, "ci8")
+            got = to_numpy_int(o)
+            np.testing.assert_array_equal(got[..., 0], ref.real.astype(np.int64))
+            np.testing.assert_array_equal(got[..., 1], ref.imag.astype(np.int64))

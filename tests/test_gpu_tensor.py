@@ -150,3 +150,14 @@ def test_precision_workload_full_size_sampled(variant):
     for p in range(2):
         assert (got8[:, autos, p, p, 1] == 0).all()
         assert (got8[:, autos, p, p, 0] > 0).all()
+
+
+def test_several_integrations_one_launch(variant):
+    """Integrations are stacked in front of the channels: [I][C][S][T][pol]."""
+    S, C, T, I = 100, 3, 96, 4
+    x8 = synth.int8_normal(synth.rng(65), (I, C, S, T, 2))
+    out = run_tc(x8, S, C, T, "ci8", I=I, expect_variant=variant)
+    got = to_numpy_int(out)
+    ref = oracle.correlate(x8.reshape(I * C, S, T, 2, 2), "ci8")
+    np.testing.assert_array_equal(got[..., 0], ref.real.astype(np.int64))
+    np.testing.assert_array_equal(got[..., 1], ref.imag.astype(np.int64))
