@@ -162,9 +162,11 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
 corr_status_t corr_destroy(corr_handle_t h);
 
 /* Tile variant the plan's tensor path uses: 0 = 64x64-station tiles,
- * 1 = 64 x up to 128 stations; -1 for FP32 plans or NULL. Chosen in
- * corr_create by timing both (see CORR_FLAG_NO_AUTOTUNE); the environment
- * variable CORR_TC_VARIANT=narrow|wide forces one. */
+ * 1 = 64 x up to 128 stations, 2 = 128x128-station tiles on a cluster of two
+ * CTAs (CTA-pair MMAs); -1 for FP32 plans or NULL. Chosen in corr_create by
+ * timing each (see CORR_FLAG_NO_AUTOTUNE); the environment variable
+ * CORR_TC_VARIANT=narrow|wide|pair forces one (pair falls back to wide where
+ * a cluster of two such CTAs cannot be resident). */
 int corr_tile_variant(corr_handle_t h);
 
 /* Reads and clears the plan's device error word (synchronous copy):

@@ -203,7 +203,7 @@ class Plan:
     # ------------------------------------------------------------- misc
     def tile_variant(self) -> str:
         v = self.L.corr_tile_variant(self.h)
-        return {0: "narrow", 1: "wide"}.get(v, "fp32")
+        return {0: "narrow", 1: "wide", 2: "pair"}.get(v, "fp32")
 
     def check_error(self):
         _check(self.L.corr_get_error(self.h), "corr_get_error")

@@ -33,9 +33,9 @@ struct corr_plan {
     // tensor path (single problem)
     int4 *d_items = nullptr;
     int n_items = 0;
-    int tc_grid = 0;
     int tc_variant = TC_NARROW;
-    float tune_ms[2] = {0.f, 0.f};
+    int pair_clusters = 0;     // clusters of the pair variant resident at once (0: unavailable)
+    float tune_ms[TC_N_VARIANTS] = {0.f, 0.f, 0.f};
     // int8 power check / redo list (single problem and batches)
     int *d_redo_mark = nullptr;
     int4 *d_redo_items = nullptr;
@@ -133,13 +133,18 @@ void fp32_config(corr_plan *h)
 // Work items of the tensor kernel: {prob, unit, rb, cb0 | ncb << 16}, row
 // block rb and column blocks cb0..cb0+ncb-1 of 64 stations, rb <= cb0.
 // narrow: every (rb, cb) with rb <= cb; wide: column blocks taken in pairs
-// from the row block onward (the last one alone if the count is odd).
+// from the row block onward (the last one alone if the count is odd); pair:
+// row blocks {rb, rb+1} x column blocks {cb0, cb0+1} for even rb <= cb0 (a
+// block past the last holds no stations). Items are unit-major.
 std::vector<int4> tc_items_for(int prob, int S, int units, int variant)
 {
     std::vector<int4> v;
     const int nb = tc_blocks(S);
     for (int u = 0; u < units; ++u) {
-        if (variant == TC_WIDE) {
+        if (variant == TC_PAIR) {
+            for (int rb = 0; rb < nb; rb += 2)
+                for (int cb = rb; cb < nb; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
+        } else if (variant == TC_WIDE) {
             for (int rb = 0; rb < nb; ++rb)
                 for (int cb = rb; cb < nb; cb += 2) {
                     const int ncb = std::min(2, nb - cb);
@@ -199,13 +204,25 @@ corr_status_t ensure_redo(corr_plan *h, int n)
 // Launches the tensor kernel for p.items[0 .. p.n_items). int8 with more than
 // one 512-sample chunk runs unchunked with the station power check, then a
 // chunked launch over the items the check rejected (usually none).
-corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, bool wide, int max_T, cudaStream_t s)
+// CTAs of a launch over up to n items: one per SM, or two per cluster of
+// the pair variant.
+int tc_grid_for(const corr_plan *h, int variant, int n)
 {
-    const int grid = std::max(1, std::min(p.n_items, h->sm_count));
+    if (variant == TC_PAIR) return 2 * std::max(1, std::min(n, h->pair_clusters));
+    return std::max(1, std::min(n, h->sm_count));
+}
+
+corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, int variant, int max_T, cudaStream_t s)
+{
+    if (variant == TC_PAIR && h->pair_clusters < 1) {
+        set_last_error("the pair tile variant does not fit on this device");
+        return CORR_ERR_UNSUPPORTED;
+    }
+    const int grid = tc_grid_for(h, variant, p.n_items);
     const bool checked = dtype == CORR_CI8 && max_T > TC_INT8_CHUNK_KB * TC_KB_T && h->redo_cap >= p.n_items;
     if (!checked) {
         p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
-        return cuda_status(tc_launch(dtype, wide, p, grid, s));
+        return cuda_status(tc_launch(dtype, variant, p, grid, s));
     }
     corr_status_t st = cuda_status(cudaMemsetAsync(h->d_redo_mark, 0, (size_t)p.n_items * sizeof(int), s));
     if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count, 0, sizeof(int), s));
@@ -216,7 +233,7 @@ corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, bool wide, int max
     a.redo_mark = h->d_redo_mark;
     a.redo_items = h->d_redo_items;
     a.redo_count = h->d_redo_count;
-    st = cuda_status(tc_launch(dtype, wide, a, grid, s));
+    st = cuda_status(tc_launch(dtype, variant, a, grid, s));
     if (st != CORR_OK) return st;
     TcParams b = p;
     b.items = h->d_redo_items;
@@ -224,7 +241,7 @@ corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, bool wide, int max
     b.n_items_dev = h->d_redo_count;
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
-    return cuda_status(tc_launch(dtype, wide, b, h->sm_count, s));
+    return cuda_status(tc_launch(dtype, variant, b, tc_grid_for(h, variant, p.n_items), s));
 }
 
 corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long long units,
@@ -251,7 +268,7 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     p.n_items = (int)((long long)h->n_items / ((long long)d.n_channels * d.n_integrations) * units);
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return run_tensor(h, p, d.dtype, h->tc_variant == TC_WIDE, d.n_samples, s);
+    return run_tensor(h, p, d.dtype, h->tc_variant, d.n_samples, s);
 }
 
 corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
@@ -268,10 +285,10 @@ size_t out_unit_bytes(const corr_desc_t &d) { return (size_t)n_baselines(d.n_sta
 
 // ------------------------------------------------------------------ autotuner
 // The tile variant of the tensor path is chosen per (device, dtype, S, T) by
-// timing both variants once on zero-filled samples of the plan's shape (about
-// four waves of work items over the SMs), unless CORR_TC_VARIANT=narrow|wide
-// forces one or CORR_FLAG_NO_AUTOTUNE asks for the heuristic (wide from 128
-// stations). Choices are cached for the process.
+// timing the variants once on zero-filled samples of the plan's shape (about
+// four waves of work items over the SMs), unless CORR_TC_VARIANT=
+// narrow|wide|pair forces one or CORR_FLAG_NO_AUTOTUNE asks for the
+// heuristic (pair from 128 stations). Choices are cached for the process.
 struct TuneKey {
     int dev, dtype, S, T;
     bool operator<(const TuneKey &o) const
@@ -288,6 +305,7 @@ int forced_variant()
     if (!e) return -1;
     if (std::strcmp(e, "wide") == 0) return TC_WIDE;
     if (std::strcmp(e, "narrow") == 0) return TC_NARROW;
+    if (std::strcmp(e, "pair") == 0) return TC_PAIR;
     return -1;
 }
 
@@ -313,11 +331,11 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
         if ((st = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
         for (int i = 0; i < 2 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, h->d.dtype, variant == TC_WIDE, T, 0);
+            st = run_tensor(h, p, h->d.dtype, variant, T, 0);
         if (st != CORR_OK) break;
         cudaEventRecord(e0, 0);
         for (int i = 0; i < 3 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, h->d.dtype, variant == TC_WIDE, T, 0);
+            st = run_tensor(h, p, h->d.dtype, variant, T, 0);
         cudaEventRecord(e1, 0);
         if (st != CORR_OK) break;
         if ((st = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
@@ -336,11 +354,11 @@ corr_status_t tune_tensor_variant(corr_plan *h)
     const corr_desc_t &d = h->d;
     const int f = forced_variant();
     if (f >= 0) {
-        h->tc_variant = f;
+        h->tc_variant = (f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f;
         return CORR_OK;
     }
     if ((d.flags & CORR_FLAG_NO_AUTOTUNE) || d.n_samples == 0) {
-        h->tc_variant = d.n_stations >= 128 ? TC_WIDE : TC_NARROW;
+        h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
         return CORR_OK;
     }
     const TuneKey key{h->device, d.dtype, d.n_stations, d.n_samples};
@@ -361,12 +379,18 @@ corr_status_t tune_tensor_variant(corr_plan *h)
     corr_status_t st = cuda_status(cudaMalloc(&d_in, in_bytes));
     if (st == CORR_OK) st = cuda_status(cudaMalloc(&d_out, out_bytes));
     if (st == CORR_OK) st = cuda_status(cudaMemset(d_in, 0, in_bytes));
-    for (int v = 0; v < 2 && st == CORR_OK; ++v)
+    for (int v = 0; v < TC_N_VARIANTS && st == CORR_OK; ++v) {
+        h->tune_ms[v] = 0.f;
+        if (v == TC_PAIR && h->pair_clusters < 1) continue;
         st = time_variant(h, v, d.n_stations, d.n_samples, su, d_in, d_out, &h->tune_ms[v]);
+    }
     cudaFree(d_in);
     cudaFree(d_out);
     if (st != CORR_OK) return st;
-    h->tc_variant = h->tune_ms[TC_WIDE] < h->tune_ms[TC_NARROW] ? TC_WIDE : TC_NARROW;
+    int best = TC_NARROW;
+    for (int v = 1; v < TC_N_VARIANTS; ++v)
+        if (h->tune_ms[v] > 0.f && h->tune_ms[v] < h->tune_ms[best]) best = v;
+    h->tc_variant = best;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = h->tc_variant;
     return CORR_OK;
@@ -481,6 +505,16 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             break;
         if ((st = cuda_status(cudaMalloc(&h->d_err, sizeof(int)))) != CORR_OK) break;
         if ((st = cuda_status(cudaMemset(h->d_err, 0, sizeof(int)))) != CORR_OK) break;
+        if (path == CORR_PATH_TENSOR) {
+            // an odd SM count or a cluster that does not fit leaves the pair
+            // variant out (0 clusters)
+            int n = 0;
+            if (tc_pair_max_clusters(d.dtype, &n) != cudaSuccess) {
+                cudaGetLastError();
+                n = 0;
+            }
+            h->pair_clusters = std::min(n, h->sm_count / 2);
+        }
         if (path == CORR_PATH_FP32) {
             fp32_config(h);
         } else {
@@ -492,7 +526,6 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             if ((st = cuda_status(cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int4),
                                              cudaMemcpyHostToDevice))) != CORR_OK)
                 break;
-            h->tc_grid = std::max(1, std::min(h->n_items, h->sm_count));
             if (d.dtype == CORR_CI8 && (st = ensure_redo(h, h->n_items)) != CORR_OK) break;
         }
         if (d.flags & CORR_FLAG_HOST_IO) {
@@ -604,7 +637,8 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
         // Build the ragged work list: tiles of all sub-arrays, heaviest (longest
         // integration) first so that the static round-robin split over the
         // persistent CTAs ends evenly. One tile variant serves the whole batch:
-        // wide when most of the work is in sub-arrays of >= 128 stations.
+        // pair (wide if pairs do not fit) when most of the work is in
+        // sub-arrays of >= 128 stations.
         {
             const int f = forced_variant();
             double big = 0, all = 0;
@@ -614,7 +648,9 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                 all += w;
                 if (subs[i].n_stations >= 128) big += w;
             }
-            h->b_variant = f >= 0 ? f : (big >= 0.5 * all ? TC_WIDE : TC_NARROW);
+            const int big_v = h->pair_clusters > 0 ? TC_PAIR : TC_WIDE;
+            h->b_variant = f >= 0 ? ((f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f)
+                                  : (big >= 0.5 * all ? big_v : TC_NARROW);
         }
         std::vector<TcProblem> probs;
         std::vector<int4> items;
@@ -664,7 +700,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     p.wait_ns = h->wait_ns;
     int max_T = 0;
     for (int i = 0; i < n_sub; ++i) max_T = std::max(max_T, subs[i].n_samples);
-    return run_tensor(h, p, h->d.dtype, h->b_variant == TC_WIDE, max_T, st);
+    return run_tensor(h, p, h->d.dtype, h->b_variant, max_T, st);
 }
 
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,

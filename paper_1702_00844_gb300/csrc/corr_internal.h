@@ -36,15 +36,21 @@ struct TcParams {
 };
 
 // Tile variants of the tensor kernel: narrow = 64x64-station tiles (N=128,
-// double-buffered accumulators); wide = 64 x up to 128 stations (N=256).
-enum TcVariant { TC_NARROW = 0, TC_WIDE = 1 };
+// double-buffered accumulators); wide = 64 x up to 128 stations (N=256);
+// pair = 128x128-station tiles on a cluster of two CTAs (CTA-pair MMAs,
+// M=256, N=256).
+enum TcVariant { TC_NARROW = 0, TC_WIDE = 1, TC_PAIR = 2 };
+constexpr int TC_N_VARIANTS = 3;
 
 constexpr int TC_RS = 64;      // stations per tile side
 constexpr int TC_KB_T = 32;    // time samples per K-block
 constexpr int TC_THREADS = 13 * 32;
 constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 
-cudaError_t tc_launch(int dtype, bool wide, const TcParams &p, int grid, cudaStream_t s);
+// grid: CTAs (even for TC_PAIR: two per cluster).
+cudaError_t tc_launch(int dtype, int variant, const TcParams &p, int grid, cudaStream_t s);
+// Clusters of the pair variant that fit on the device at once.
+cudaError_t tc_pair_max_clusters(int dtype, int *n);
 
 // ------------------------------------------------------------------ FP32 path
 struct Fp32Params {

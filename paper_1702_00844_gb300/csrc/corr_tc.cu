@@ -19,6 +19,14 @@
 // "wide"), starting at or after the row block. A persistent CTA per SM walks
 // its share of the (problem, channel, tile) list.
 //
+// "pair": a cluster of two CTAs on two SMs works on one 128 x 128-station
+// tile with CTA-pair MMAs (M = 256, N = 256): each CTA stages its own row
+// block (rb + rank) and one of the two column blocks (cb0 + rank), so per SM
+// the tensor core reads half as much B per MMA as in "wide" and the
+// producers stage two blocks per K-block instead of three. Each CTA's TMEM
+// holds its row block against both column blocks; each CTA stores its own
+// rows. Work items are taken per cluster.
+//
 // Warp roles (416 threads):
 //   warps 0-7  : stage raw samples with 16-byte asynchronous copies into a
 //                per-thread ring in shared memory (each thread later converts
@@ -32,8 +40,8 @@
 //                [channel][baseline][p1][p2] once (int8: fold each 512-sample
 //                chunk into INT32 exactly);
 //   warp 12    : allocates TMEM (narrow: 2 accumulator buffers x (Re 128 +
-//                Im 128) columns; wide: 1 buffer x (Re 256 + Im 256)) and
-//                issues the MMAs (one thread).
+//                Im 128) columns; wide and pair: 1 buffer x (Re 256 + Im 256))
+//                and issues the MMAs (one thread; in a pair, of the even CTA).
 // Every wait is bounded (see mbar_wait_bounded).
 #include "corr_internal.h"
 #include "ptx.cuh"
@@ -69,28 +77,46 @@ template <int DT> struct RawBytes { static constexpr int value = DT == 1 ? 64 : 
 #ifndef CORR_TC_RAW_I8
 #define CORR_TC_RAW_I8 5
 #endif
+#ifndef CORR_TC_OPS_PAIR_F16
+#define CORR_TC_OPS_PAIR_F16 4
+#endif
+#ifndef CORR_TC_RAW_PAIR_F16
+#define CORR_TC_RAW_PAIR_F16 2
+#endif
+#ifndef CORR_TC_OPS_PAIR_I8
+#define CORR_TC_OPS_PAIR_I8 4
+#endif
+#ifndef CORR_TC_RAW_PAIR_I8
+#define CORR_TC_RAW_PAIR_I8 5
+#endif
 constexpr int MAX_OPS = 4; // size of the stage barrier arrays
-template <int DT, bool WIDE> struct Cfg;
-template <> struct Cfg<1, false> {
+template <int DT, int V> struct Cfg;
+template <> struct Cfg<1, TC_NARROW> {
     static constexpr int OPS = CORR_TC_OPS_F16, RAW = CORR_TC_RAW_F16, MAXB = 1, NBUF = 2;
 };
-template <> struct Cfg<2, false> {
+template <> struct Cfg<2, TC_NARROW> {
     static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, MAXB = 1, NBUF = 2;
 };
-template <> struct Cfg<1, true> { static constexpr int OPS = 2, RAW = 2, MAXB = 2, NBUF = 1; };
-template <> struct Cfg<2, true> { static constexpr int OPS = 3, RAW = 3, MAXB = 2, NBUF = 1; };
+template <> struct Cfg<1, TC_WIDE> { static constexpr int OPS = 2, RAW = 2, MAXB = 2, NBUF = 1; };
+template <> struct Cfg<2, TC_WIDE> { static constexpr int OPS = 3, RAW = 3, MAXB = 2, NBUF = 1; };
+template <> struct Cfg<1, TC_PAIR> {
+    static constexpr int OPS = CORR_TC_OPS_PAIR_F16, RAW = CORR_TC_RAW_PAIR_F16, MAXB = 1, NBUF = 1;
+};
+template <> struct Cfg<2, TC_PAIR> {
+    static constexpr int OPS = CORR_TC_OPS_PAIR_I8, RAW = CORR_TC_RAW_PAIR_I8, MAXB = 1, NBUF = 1;
+};
 
-template <int DT, bool WIDE> __host__ __device__ constexpr int stage_bytes()
+template <int DT, int V> __host__ __device__ constexpr int stage_bytes()
 {
-    return (1 + Cfg<DT, WIDE>::MAXB) * TILE_BYTES;
+    return (1 + Cfg<DT, V>::MAXB) * TILE_BYTES;
 }
-template <int DT, bool WIDE> __host__ __device__ constexpr int raw_stage_bytes()
+template <int DT, int V> __host__ __device__ constexpr int raw_stage_bytes()
 {
-    return (1 + Cfg<DT, WIDE>::MAXB) * RawBytes<DT>::value * N_PRODUCERS;
+    return (1 + Cfg<DT, V>::MAXB) * RawBytes<DT>::value * N_PRODUCERS;
 }
-template <int DT, bool WIDE> __host__ __device__ constexpr int smem_bytes()
+template <int DT, int V> __host__ __device__ constexpr int smem_bytes()
 {
-    return Cfg<DT, WIDE>::OPS * stage_bytes<DT, WIDE>() + Cfg<DT, WIDE>::RAW * raw_stage_bytes<DT, WIDE>();
+    return Cfg<DT, V>::OPS * stage_bytes<DT, V>() + Cfg<DT, V>::RAW * raw_stage_bytes<DT, V>();
 }
 
 struct Bars {
@@ -103,12 +129,13 @@ struct Bars {
     int abort_flag;
 };
 
-template <int DT, bool WIDE> constexpr bool cfg_ok()
+template <int DT, int V> constexpr bool cfg_ok()
 {
-    return Cfg<DT, WIDE>::OPS >= 2 && Cfg<DT, WIDE>::OPS <= MAX_OPS && Cfg<DT, WIDE>::RAW >= 2 &&
-           smem_bytes<DT, WIDE>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
+    return Cfg<DT, V>::OPS >= 2 && Cfg<DT, V>::OPS <= MAX_OPS && Cfg<DT, V>::RAW >= 2 &&
+           smem_bytes<DT, V>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
 }
-static_assert(cfg_ok<1, false>() && cfg_ok<2, false>() && cfg_ok<1, true>() && cfg_ok<2, true>(),
+static_assert(cfg_ok<1, TC_NARROW>() && cfg_ok<2, TC_NARROW>() && cfg_ok<1, TC_WIDE>() &&
+                  cfg_ok<2, TC_WIDE>() && cfg_ok<1, TC_PAIR>() && cfg_ok<2, TC_PAIR>(),
               "stage counts must fit the barrier arrays and shared memory");
 
 template <int DT> struct Raw;          // raw samples of 8 times of one station
@@ -315,49 +342,64 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
     }
 }
 
-template <int DT, bool WIDE>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
+template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
 {
-    using C = Cfg<DT, WIDE>;
+    using C = Cfg<DT, V>;
+    constexpr bool PAIR = V == TC_PAIR;
+    constexpr bool N256 = V != TC_NARROW;          // tiles of two column blocks
     constexpr int OPS = C::OPS;
     constexpr int RAW = C::RAW;
     constexpr int NBUF = C::NBUF;
-    constexpr uint32_t STAGE = stage_bytes<DT, WIDE>();
-    constexpr uint32_t IMOFF = WIDE ? 256 : 128;   // TMEM column of Im relative to Re
-    constexpr uint32_t BUFCOLS = WIDE ? 0 : 256;   // TMEM columns between buffers
+    constexpr uint32_t STAGE = stage_bytes<DT, V>();
+    constexpr uint32_t IMOFF = N256 ? 256 : 128;   // TMEM column of Im relative to Re
+    constexpr uint32_t BUFCOLS = N256 ? 0 : 256;   // TMEM columns between buffers
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t tiles_u32 = smem_u32(smem);
     const uint32_t raw_base = tiles_u32 + OPS * STAGE;
-    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, WIDE>());
+    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, V>());
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
+    // A pair (cluster of 2 CTAs) shares each work item; rank 0 issues the MMAs.
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int item0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int item_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
+    // In a pair, the even CTA's full and acc_empty barriers also count one
+    // arrival of the odd CTA's relay thread (see the relay below).
+    const uint32_t relay = PAIR && leader ? 1u : 0u;
     if (tid == 0) {
         for (int s = 0; s < OPS; ++s) {
-            mbar_init(&bars->full[s], N_PRODUCERS);
+            mbar_init(&bars->full[s], N_PRODUCERS + relay);
             mbar_init(&bars->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], N_EPILOGUE);
+            mbar_init(&bars->acc_empty[b], N_EPILOGUE + relay);
         }
         mbar_init(&bars->fin, 1);
         bars->abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == WARP_MMA) {
-        tmem_alloc(&bars->tmem_base, TMEM_COLS);
-        tmem_relinquish();
+        if constexpr (PAIR) {
+            tmem_alloc_pair(&bars->tmem_base, TMEM_COLS);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(&bars->tmem_base, TMEM_COLS);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync(); // both CTAs' barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem_base = bars->tmem_base;
 
@@ -375,12 +417,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         constexpr int NSLOT = 1 + C::MAXB;
         int stage = 0;
         uint32_t phase = 0;
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        for (int it = item0; it < n_items; it += item_step) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const bool diag = item.cb0 == item.rb;
-            const int nB = item.ncb - (diag ? 1 : 0);          // B blocks to stage
-            const int b_first = diag ? item.cb0 + 1 : item.cb0;
+            // B blocks to stage and the first of them; a pair CTA stages
+            // column block cb0 + rank (none on the diagonal: it is its A).
+            const int nB = PAIR ? (diag ? 0 : 1) : item.ncb - (diag ? 1 : 0);
+            const int b_first = PAIR ? item.cb0 + (int)rank : (diag ? item.cb0 + 1 : item.cb0);
             const uint8_t *unit_in = static_cast<const uint8_t *>(P.in) +
                                      (size_t)item.unit * (size_t)P.in_unit_bytes;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
@@ -390,7 +434,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
 #pragma unroll
             for (int j = 0; j < NSLOT; ++j) power[j] = 0;
             int st_of[NSLOT];
-            st_of[0] = item.rb * TC_RS + sl;
+            st_of[0] = (item.rb + (int)rank) * TC_RS + sl;
 #pragma unroll
             for (int j = 1; j < NSLOT; ++j) st_of[j] = (b_first + j - 1) * TC_RS + sl;
             auto slot_addr = [&](int k, int j) {
@@ -476,12 +520,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
         const int p1 = row & 1;
         uint32_t acc_it = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (int it = item0; it < n_items && ok; it += item_step) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const int nch = n_chunks(nkb, p.chunk_kb);
-            const int s1 = item.rb * TC_RS + sl;
+            const int s1 = (item.rb + (int)rank) * TC_RS + sl;
             const int ngroups = 8 * item.ncb;  // groups of 8 column stations
             const long long unit_off = (long long)item.unit * P.out_unit_elems + p1 * 2;
             for (int c = 0; c < nch; ++c, ++acc_it) {
@@ -523,21 +567,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                 mbar_arrive(&bars->acc_empty[buf]);
             }
         }
-    } else {
+    } else if (leader) {
         // ------------------------------------------------------------ MMA
-        constexpr uint32_t ID128 = idesc_f16_f32(128, 128, false);
-        constexpr uint32_t ID128N = idesc_f16_f32(128, 128, true);
-        constexpr uint32_t ID256 = idesc_f16_f32(128, 256, false);
-        constexpr uint32_t ID256N = idesc_f16_f32(128, 256, true);
+        // M = 256 for a pair (128 rows from each CTA), else 128.
+        constexpr int M = PAIR ? 256 : 128;
+        constexpr uint32_t ID128 = idesc_f16_f32(M, 128, false);
+        constexpr uint32_t ID128N = idesc_f16_f32(M, 128, true);
+        constexpr uint32_t ID256 = idesc_f16_f32(M, 256, false);
+        constexpr uint32_t ID256N = idesc_f16_f32(M, 256, true);
         int stage = 0;
         uint32_t phase = 0;
         uint32_t acc_it = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        auto mma = [&](uint32_t d, uint32_t a, uint32_t b, uint32_t id, uint32_t acc) {
+            if constexpr (PAIR)
+                tc_mma_f16_pair(d, smem_desc_sw128(a), smem_desc_sw128(b), id, acc);
+            else
+                tc_mma_f16(d, smem_desc_sw128(a), smem_desc_sw128(b), id, acc);
+        };
+        auto commit = [&](uint64_t *bar) {
+            if constexpr (PAIR)
+                tc_commit_pair(bar, 3);   // the barrier at this offset in both CTAs
+            else
+                tc_commit(bar);
+        };
+        for (int it = item0; it < n_items && ok; it += item_step) {
             const Item item = get_item(p, it);
             const TcProblem P = get_prob(p, item.prob);
             const bool diag = item.cb0 == item.rb;
-            const bool n256 = WIDE && item.ncb == 2;
+            const bool n256 = N256 && item.ncb == 2;
             const uint32_t idesc = n256 ? ID256 : ID128;
             const uint32_t idesc_neg = n256 ? ID256N : ID128N;
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
@@ -545,8 +603,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
             const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
             for (int c = 0; c < nch && ok; ++c, ++acc_it) {
                 const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
-                if (!mbar_wait_bounded(&bars->acc_empty[buf], ap ^ 1, abort_flag, p.err,
-                                       p.wait_ns)) {
+                if (!mbar_wait_bounded<PAIR>(&bars->acc_empty[buf], ap ^ 1, abort_flag, p.err,
+                                             p.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -556,8 +614,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                 const int kb_lo = c * ckb;
                 const int kb_hi = min(nkb, kb_lo + ckb);
                 for (int kb = kb_lo; kb < kb_hi; ++kb) {
-                    if (!mbar_wait_bounded(&bars->full[stage], phase, abort_flag, p.err,
-                                           p.wait_ns)) {
+                    if (!mbar_wait_bounded<PAIR>(&bars->full[stage], phase, abort_flag, p.err,
+                                                 p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -568,15 +626,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                         const uint32_t first = kb == kb_lo ? 1u : 0u;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks)
-                            tc_mma_f16(d_re, smem_desc_sw128(a + 32 * ks),
-                                       smem_desc_sw128(b + 32 * ks), idesc,
-                                       (first && ks == 0) ? 0u : 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 64), smem_desc_sw128(b + 0), idesc,
-                                   first ? 0u : 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 96), smem_desc_sw128(b + 32), idesc, 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 0), smem_desc_sw128(b + 64), idesc_neg, 1u);
-                        tc_mma_f16(d_im, smem_desc_sw128(a + 32), smem_desc_sw128(b + 96), idesc_neg, 1u);
-                        tc_commit(&bars->empty[stage]);
+                            mma(d_re, a + 32 * ks, b + 32 * ks, idesc, (first && ks == 0) ? 0u : 1u);
+                        mma(d_im, a + 64, b + 0, idesc, first ? 0u : 1u);
+                        mma(d_im, a + 96, b + 32, idesc, 1u);
+                        mma(d_im, a + 0, b + 64, idesc_neg, 1u);
+                        mma(d_im, a + 32, b + 96, idesc_neg, 1u);
+                        commit(&bars->empty[stage]);
                     }
                     __syncwarp();
                     if (++stage == OPS) {
@@ -585,43 +640,147 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
                     }
                 }
                 if (!ok) break;
-                if (lane == 0) tc_commit(&bars->acc_full[buf]);
+                if (lane == 0) commit(&bars->acc_full[buf]);
                 __syncwarp();
             }
         }
-        // Wait for every MMA this thread issued before TMEM is freed. This wait
+        // Wait for every MMA this thread issued before TMEM is freed (and, in
+        // a pair, before the odd CTA's shared memory can go away). This wait
         // keeps a fixed 2 s bound whatever p.wait_ns is, so that an aborted
         // kernel never frees TMEM under a running MMA.
-        if (lane == 0) tc_commit(&bars->fin);
+        if (lane == 0) commit(&bars->fin);
         __syncwarp();
         int dummy_abort = 0;
         mbar_wait_bounded(&bars->fin, 0, &dummy_abort, p.err, 2000000000ull);
+    } else if constexpr (PAIR) {
+        // ------------------------------------------ relay (odd CTA of a pair)
+        // This CTA's producers and epilogue arrive on its own barriers (CTA
+        // scope, as in a single CTA: a cluster-scope release in every
+        // producer thread would also wait for its asynchronous copies in
+        // flight). One thread follows the MMA thread's order of waits and
+        // forwards each completed phase to the even CTA with one
+        // cluster-scope arrival: the K-blocks of a chunk, then the release
+        // of the accumulator after this CTA's epilogue has read it.
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t acc_it = 0;
+            bool ok = true;
+            for (int it = item0; it < n_items && ok; it += item_step) {
+                const Item item = get_item(p, it);
+                const TcProblem P = get_prob(p, item.prob);
+                const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
+                const int nch = n_chunks(nkb, p.chunk_kb);
+                const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
+                for (int c = 0; c < nch && ok; ++c, ++acc_it) {
+                    const int kb_lo = c * ckb;
+                    const int kb_hi = min(nkb, kb_lo + ckb);
+                    for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                        if (!mbar_wait_bounded(&bars->full[stage], phase, abort_flag, p.err, p.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_cluster(mapa_shared(smem_u32(&bars->full[stage]), 0));
+                        if (++stage == OPS) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (!ok) break;
+                    const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
+                    if (!mbar_wait_bounded(&bars->acc_empty[buf], ap, abort_flag, p.err, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars->acc_empty[buf]), 0));
+                }
+            }
+        }
+        __syncwarp();
     }
 
     tc_fence_before();
     __syncthreads();
+    // A pair leaves together: the even CTA has seen its MMAs complete, and the
+    // odd CTA's remote arrivals have all been made.
+    if constexpr (PAIR) cluster_sync();
     if (warp == WARP_MMA) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, TMEM_COLS);
+        if constexpr (PAIR)
+            tmem_dealloc_pair(tmem_base, TMEM_COLS);
+        else
+            tmem_dealloc(tmem_base, TMEM_COLS);
     }
 }
 
-template <int DT, bool WIDE> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
+template <int DT, int V>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
 {
-    const size_t smem = (size_t)smem_bytes<DT, WIDE>() + sizeof(Bars) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(tc_correlate_kernel<DT, WIDE>,
+    tc_correlate_body<DT, V>(p);
+}
+
+template <int DT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    tc_pair_kernel(const __grid_constant__ TcParams p)
+{
+    tc_correlate_body<DT, TC_PAIR>(p);
+}
+
+template <int DT, int V> const void *kernel_ptr()
+{
+    if constexpr (V == TC_PAIR)
+        return reinterpret_cast<const void *>(&tc_pair_kernel<DT>);
+    else
+        return reinterpret_cast<const void *>(&tc_correlate_kernel<DT, V>);
+}
+
+template <int DT, int V> size_t smem_total() { return (size_t)smem_bytes<DT, V>() + sizeof(Bars) + 1024; }
+
+template <int DT, int V> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
+{
+    const size_t smem = smem_total<DT, V>();
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tc_correlate_kernel<DT, WIDE><<<grid, TC_THREADS, smem, s>>>(p);
+    if constexpr (V == TC_PAIR)
+        tc_pair_kernel<DT><<<grid, TC_THREADS, smem, s>>>(p);
+    else
+        tc_correlate_kernel<DT, V><<<grid, TC_THREADS, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int DT> cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s)
+{
+    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR>(p, grid, s);
+    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE>(p, grid, s);
+    return launch_one<DT, TC_NARROW>(p, grid, s);
+}
+
+template <int DT> cudaError_t pair_clusters_dt(int *n)
+{
+    const size_t smem = smem_total<DT, TC_PAIR>();
+    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    return cudaOccupancyMaxActiveClusters(n, tc_pair_kernel<DT>, &cfg);
 }
 
 } // namespace
 
-cudaError_t tc_launch(int dtype, bool wide, const TcParams &p, int grid, cudaStream_t s)
+cudaError_t tc_launch(int dtype, int variant, const TcParams &p, int grid, cudaStream_t s)
 {
-    if (dtype == 1) return wide ? launch_one<1, true>(p, grid, s) : launch_one<1, false>(p, grid, s);
-    return wide ? launch_one<2, true>(p, grid, s) : launch_one<2, false>(p, grid, s);
+    if (variant == TC_PAIR && (grid < 2 || grid % 2 != 0)) return cudaErrorInvalidValue;
+    return dtype == 1 ? launch_dt<1>(variant, p, grid, s) : launch_dt<2>(variant, p, grid, s);
+}
+
+cudaError_t tc_pair_max_clusters(int dtype, int *n)
+{
+    *n = 0;
+    return dtype == 1 ? pair_clusters_dt<1>(n) : pair_clusters_dt<2>(n);
 }
 
 } // namespace corr

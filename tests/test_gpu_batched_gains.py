@@ -48,7 +48,7 @@ def check_batch(dtype, outs, hosts):
             assert rel_frobenius_per_unit(got, ref).max() < TOL_FP16
 
 
-@pytest.mark.parametrize("variant", ["narrow", "wide"])
+@pytest.mark.parametrize("variant", ["narrow", "wide", "pair"])
 @pytest.mark.parametrize("dtype", ["cf16", "ci8"])
 def test_ragged_batch_one_launch(dtype, variant, monkeypatch):
     monkeypatch.setenv("CORR_TC_VARIANT", variant)
@@ -204,7 +204,7 @@ def test_ragged_int8_batch_with_extreme_subarray_takes_redo_path(monkeypatch):
         xs.append(torch.from_numpy(h).cuda())
         outs.append(torch.full((C, S * (S + 1) // 2, 2, 2, 2), 0x7FFFFFFF, dtype=torch.int32,
                                device="cuda"))
-    for variant in ("narrow", "wide"):
+    for variant in ("narrow", "wide", "pair"):
         monkeypatch.setenv("CORR_TC_VARIANT", variant)
         plan = Plan(1, 1, 1, dtype="ci8", path="tensor")
         plan.correlate_batched(list(zip(xs, outs)), shapes)

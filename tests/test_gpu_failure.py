@@ -15,11 +15,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_tensor_wait_timeout_is_reported_and_context_survives(monkeypatch):
+@pytest.mark.parametrize("variant", ["narrow", "pair"])
+def test_tensor_wait_timeout_is_reported_and_context_survives(monkeypatch, variant):
+    """narrow: one CTA gives up; pair: either CTA of a cluster gives up and
+    the other runs into its own limits, both meet at the final cluster
+    barrier."""
     from paper_1702_00844_gb300 import CorrError, Plan
     S, C, T = 256, 24, 4096   # each tile's epilogue waits ~100 us for its MMAs
     monkeypatch.setenv("CORR_WAIT_LIMIT_NS", "1")
-    monkeypatch.setenv("CORR_TC_VARIANT", "narrow")
+    monkeypatch.setenv("CORR_TC_VARIANT", variant)
     plan = Plan(S, C, T, dtype="cf16", path="tensor")
     x = torch.zeros((C, S, T, 2, 2), dtype=torch.float16, device="cuda")
     plan.correlate(x)
