@@ -402,7 +402,8 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": profiled_traffic() if wl == "precision" else None,
-                "kernel": f"tc_correlate_kernel<{dtype_label}, {plan.tile_variant()}>",
+                "kernel": (f"tc_pair_kernel<{dtype_label}> (CTA pairs)" if plan.tile_variant() == "pair"
+                           else f"tc_correlate_kernel<{dtype_label}, {plan.tile_variant()}>"),
                 "peak_source": f"{peak_src} bf16 dense burst (f16 dense runs at the bf16 rate)"}
     roof["algorithmic_bytes"] = alg_bytes
     roof["hbm_bound_TOPS"] = ops / (alg_bytes / (hbm * 1e9)) / 1e12

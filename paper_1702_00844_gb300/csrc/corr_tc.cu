@@ -539,11 +539,14 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                 const bool last = c == nch - 1;
                 // Column groups of 16 TMEM columns (8 column stations x 2 pols),
                 // Re and Im; the load of the next group overlaps the stores of
-                // the current one (two register sets).
+                // the current one (two register sets). The accumulator is
+                // released as soon as its last columns are in registers, so the
+                // last group's stores overlap the next MMAs.
                 uint32_t ra[16], ia[16], rb2[16], ib2[16];
                 tmem_ld_32x32b_x16(taddr, ra);
                 tmem_ld_32x32b_x16(taddr + IMOFF, ia);
                 tmem_wait_ld();
+                bool released = false;
 #pragma unroll 1
                 for (int cc = 0; cc < ngroups; cc += 2) {
                     const bool has1 = cc + 1 < ngroups;
@@ -553,6 +556,11 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                     }
                     store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
                     tmem_wait_ld();
+                    if (cc + 2 >= ngroups) {  // every column of this chunk has been read
+                        tc_fence_before();
+                        mbar_arrive(&bars->acc_empty[buf]);
+                        released = true;
+                    }
                     if (has1) {
                         if (cc + 2 < ngroups) {
                             tmem_ld_32x32b_x16(taddr + (cc + 2) * 16, ra);
@@ -560,11 +568,13 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                         }
                         store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + (cc + 1) * 8, c > 0, last,
                                         rb2, ib2);
-                        tmem_wait_ld();
+                        if (cc + 2 < ngroups) tmem_wait_ld();
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(&bars->acc_empty[buf]);
+                if (!released) {
+                    tc_fence_before();
+                    mbar_arrive(&bars->acc_empty[buf]);
+                }
             }
         }
     } else if (leader) {
