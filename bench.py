@@ -298,6 +298,25 @@ def secondary(x8, torch):
 
     ms = time_launches(step, 10, 3, st)
     res["gain_forward_backward_differentiation"] = {"ms": ms}
+    del pg, xd, gd, Md, R, gg, gx
+    torch.cuda.empty_cache()
+    # sample layouts (corr_reorder) on the int8 precision samples: the
+    # time-major layout of Section 4.4 and the per-station streams before the
+    # corner turn of Section 7, each into the correlator's layout. HBM-bound:
+    # every byte read once and written once.
+    from paper_1702_00844_gb300 import reorder
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    nbytes = x8.numel() * x8.element_size()
+    x6 = x8.view(1, C3, S3, T3, 2, 2)
+    for L in ("cts", "sct"):
+        other = reorder(x6, S3, C3, T3, 1, "ci8", "cst", L)
+        back = torch.empty_like(x6)
+        ms = time_launches(lambda: reorder(other, S3, C3, T3, 1, "ci8", L, "cst", out=back), 10, 3, st)
+        gbs = 2 * nbytes / (ms * 1e-3) / 1e9
+        res[f"reorder_{L}_to_cst_int8"] = {"ms": ms, "GB/s": gbs, "hbm_frac": gbs / hbm,
+                                           "peak": f"{src} hbm_gbs {hbm:.0f}"}
+        del other, back
     return res
 
 

@@ -161,6 +161,30 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
  * NULL is accepted. */
 corr_status_t corr_destroy(corr_handle_t h);
 
+/* Sample layouts of one integration (integrations are always outermost; an
+ * element is both pols of one complex sample, [pol][re, im]):
+ *   CORR_LAYOUT_CST  [channel][station][time]: what corr_correlate reads;
+ *   CORR_LAYOUT_CTS  [channel][time][station]: all stations of one time step
+ *                    together, the transposed layout of Section 4.4 (Fig. 4);
+ *   CORR_LAYOUT_SCT  [station][channel][time]: one receiver's stream with all
+ *                    its channels, the input of the FX corner turn
+ *                    (Section 7). */
+typedef enum { CORR_LAYOUT_CST = 0, CORR_LAYOUT_CTS = 1, CORR_LAYOUT_SCT = 2 } corr_layout_t;
+
+/* Permutes samples from layout `from` to layout `to` on the device, bit for
+ * bit (Section 4.4's transpose and the local part of Section 7's corner
+ * turn). Needs no plan and allocates nothing; asynchronous on `stream`.
+ *   d_in, d_out: device buffers of n_integrations * n_channels * n_stations *
+ *       n_samples elements of dtype (4 bytes for CORR_CI8, 8 for CORR_CF16,
+ *       16 for CORR_CF32), aligned to the element size; they must not
+ *       overlap. May be NULL when there are no elements.
+ * Errors: CORR_ERR_INVALID_ARG for negative sizes, n_integrations < 1, an
+ * unknown dtype or layout, NULL, misaligned or overlapping buffers;
+ * CORR_ERR_CUDA if the launch fails. */
+corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_integrations,
+                           corr_dtype_t dtype, corr_layout_t from, corr_layout_t to,
+                           const void *d_in, void *d_out, void *stream);
+
 /* Tile variant the plan's tensor path uses: 0 = 64x64-station tiles,
  * 1 = 64 x up to 128 stations, 2 = 128x128-station tiles on a cluster of two
  * CTAs (CTA-pair MMAs); -1 for FP32 plans or NULL. Chosen in corr_create by

@@ -16,7 +16,9 @@ Functions with a pin (tests under ``tests/test_oracle_pins.py``):
                       channel independence), exact integers;
   * ``gain_loss``   - brute-force definition on tiny inputs;
   * ``gain_grad``   - central finite differences of ``gain_loss``;
-  * ``input_grad``  - central finite differences through ``correlate``.
+  * ``input_grad``  - central finite differences through ``correlate``;
+  * ``reorder``     - element placement built by plain loops from each
+                      layout's definition, round trips, composition.
 """
 from __future__ import annotations
 
@@ -129,3 +131,19 @@ def input_grad(x: np.ndarray, R: np.ndarray, g: np.ndarray, M: np.ndarray) -> np
     out = np.zeros_like(x)
     _load().oracle_input_grad(_ptr(x), _ptr(R), _ptr(g), _ptr(M), units, S, T, P, _ptr(out))
     return out
+
+
+# Axes of one integration in each sample layout (Section 4.4's transposed
+# layout keeps all stations of a time step together; Section 7's corner turn
+# starts from one receiver's stream of all channels).
+LAYOUT_AXES = {"cst": ("c", "s", "t"), "cts": ("c", "t", "s"), "sct": ("s", "c", "t")}
+
+
+def reorder(x: np.ndarray, from_layout: str, to_layout: str) -> np.ndarray:
+    """Samples x[I][three axes of from_layout][...element] rearranged into
+    to_layout: element (i, c, s, t) keeps its value and moves to its place in
+    the new axis order (a numpy transpose of the three layout axes)."""
+    src = LAYOUT_AXES[from_layout]
+    dst = LAYOUT_AXES[to_layout]
+    perm = [0] + [1 + src.index(a) for a in dst] + list(range(4, x.ndim))
+    return np.ascontiguousarray(np.transpose(x, perm))

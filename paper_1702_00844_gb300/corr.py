@@ -18,6 +18,7 @@ PATHS = {"auto": 0, "fp32": 1, "tensor": 2}
 FLAG_GAINS = 0x1
 FLAG_NO_AUTOTUNE = 0x2
 FLAG_HOST_IO = 0x4
+LAYOUTS = {"cst": 0, "cts": 1, "sct": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory",
           4: "CUDA error", 5: "timeout"}
 
@@ -77,6 +78,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_fp32_subtile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_gain_backward_noalloc.argtypes = [ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.corr_gain_backward_noalloc.restype = ip
+    L.corr_reorder.argtypes = [ip, ip, ip, ip, ip, ip, ip, vp, vp, vp]
+    L.corr_reorder.restype = ip
     L.corr_noalloc_scratch_bytes.argtypes = []
     L.corr_noalloc_scratch_bytes.restype = ctypes.c_size_t
     for name in ("corr_create", "corr_correlate", "corr_correlate_host", "corr_correlate_batched", "corr_gain_loss",
@@ -108,6 +111,32 @@ def _ptr(t: Optional[torch.Tensor]):
     if not t.is_contiguous():
         raise ValueError("contiguous tensor expected")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def layout_shape(S: int, C: int, T: int, I: int, dtype: str, layout: str):
+    """Tensor shape of samples in a layout: [I] + the layout's three axes +
+    [2 pols] (+ [re, im] for the f16 and int8 types)."""
+    axes = {"cst": (C, S, T), "cts": (C, T, S), "sct": (S, C, T)}[layout]
+    base = (I,) + axes + (2,)
+    return base if dtype == "cf32" else base + (2,)
+
+
+def reorder(x: torch.Tensor, S: int, C: int, T: int, I: int, dtype: str, from_layout: str,
+            to_layout: str, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """``corr_reorder``: samples ``x`` in layout ``from_layout`` ("cst", "cts" or
+    "sct") permuted into ``to_layout`` on the device."""
+    L = lib()
+    if out is None:
+        out = torch.empty(layout_shape(S, C, T, I, dtype, to_layout), dtype=torch_dtype(dtype),
+                          device=x.device)
+    want = I * C * S * T * 2 * (1 if dtype == "cf32" else 2)
+    for t, what in ((x, "samples"), (out, "out")):
+        if t.numel() != want or t.dtype != torch_dtype(dtype):
+            raise ValueError(f"{what}: expected {want} elements of {torch_dtype(dtype)}")
+    _check(L.corr_reorder(S, C, T, I, DTYPES[dtype], LAYOUTS[from_layout], LAYOUTS[to_layout],
+                          _ptr(x), _ptr(out), ctypes.c_void_p(_stream_handle(stream))),
+           "corr_reorder")
+    return out
 
 
 def n_baselines(S: int) -> int:

@@ -749,6 +749,32 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     return e;
 }
 
+corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_integrations,
+                           corr_dtype_t dtype, corr_layout_t from, corr_layout_t to,
+                           const void *d_in, void *d_out, void *stream)
+{
+    if (n_stations < 0 || n_channels < 0 || n_samples < 0 || n_integrations < 1)
+        return CORR_ERR_INVALID_ARG;
+    if (dtype < CORR_CF32 || dtype > CORR_CI8) return CORR_ERR_INVALID_ARG;
+    if (from < CORR_LAYOUT_CST || from > CORR_LAYOUT_SCT || to < CORR_LAYOUT_CST || to > CORR_LAYOUT_SCT)
+        return CORR_ERR_INVALID_ARG;
+    const int eb = bytes_per_sample(dtype);
+    const unsigned long long elems =
+        (unsigned long long)n_integrations * n_channels * n_stations * n_samples;
+    if (elems == 0) return CORR_OK;
+    if (!d_in || !d_out) return CORR_ERR_INVALID_ARG;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
+    if (a % eb != 0 || b % eb != 0) return CORR_ERR_INVALID_ARG;
+    const unsigned long long bytes = elems * eb;
+    if (a < b + bytes && b < a + bytes) return CORR_ERR_INVALID_ARG; // overlap
+    int dev = 0, sms = 0;
+    corr_status_t st = cuda_status(cudaGetDevice(&dev));
+    if (st == CORR_OK) st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (st != CORR_OK) return st;
+    return cuda_status(reorder_launch(d_in, d_out, n_stations, n_channels, n_samples, n_integrations,
+                                      eb, from, to, sms, static_cast<cudaStream_t>(stream)));
+}
+
 int corr_tile_variant(corr_handle_t h)
 {
     if (!h) return -1;

@@ -75,6 +75,12 @@ cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
                               const float2 *M, const float *scale, float2 *W,
                               float2 *grad_x, int S, int T, int units, cudaStream_t s);
 
+// ------------------------------------------------------------ layouts
+// Permutes n_integrations x (C x S x T) elements of elem_bytes (4, 8 or 16)
+// from layout `from` to layout `to` (corr_layout_t).
+cudaError_t reorder_launch(const void *in, void *out, int S, int C, int T, long long n_integrations,
+                           int elem_bytes, int from, int to, int sm_count, cudaStream_t s);
+
 // Records the text returned by corr_last_error_message on this thread.
 void set_last_error(cudaError_t e);
 void set_last_error(const char *msg);

@@ -127,3 +127,17 @@ def test_global_arithmetic_intensity():
     assert ai_global(64) == 65
     assert correlator_ops(8, 256, 16) == 32 * 36 * 256 * 16
     assert correlator_ops(256, 1024, 480) == pytest.approx(5.174e11, rel=1e-3)
+
+
+def test_reorder_rejects_bad_arguments_without_gpu(L):
+    """corr_reorder's argument checks run before any CUDA call."""
+    a, b = ctypes.c_void_p(4096), ctypes.c_void_p(1 << 30)
+    ok_args = (8, 2, 16, 1, 2, 0, 1)          # S, C, T, I, ci8, cst -> cts
+    bad = [(-1, 2, 16, 1, 2, 0, 1), (8, 2, 16, 0, 2, 0, 1), (8, 2, 16, 1, 3, 0, 1),
+           (8, 2, 16, 1, 2, 3, 1), (8, 2, 16, 1, 2, 0, -1)]
+    for args in bad:
+        assert L.corr_reorder(*args, a, b, None) == 1
+    assert L.corr_reorder(*ok_args, None, b, None) == 1                  # NULL input
+    assert L.corr_reorder(*ok_args, ctypes.c_void_p(4098), b, None) == 1  # misaligned (4-byte elements)
+    assert L.corr_reorder(*ok_args, a, ctypes.c_void_p(4096 + 64), None) == 1  # overlapping
+    assert L.corr_reorder(0, 2, 16, 1, 2, 0, 1, None, None, None) == 0   # nothing to move

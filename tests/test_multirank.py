@@ -74,3 +74,58 @@ def test_two_ranks_gloo(tmp_path):
     tmax = float(open(tmp_path / "tmax.txt").read())
     assert tmax == 1.5
     assert job_throughput([3, 5], tmax) == pytest.approx(8 / 1.5)
+
+
+def _np_reorder(x, S, C, T, I, dtype, a, b):
+    """Test stand-in for corr_reorder on CPU tensors (the oracle's permutation)."""
+    import torch
+
+    import oracle
+    return torch.from_numpy(oracle.reorder(x.numpy(), a, b))
+
+
+def _corner_worker(rank, world, port, out_dir, dtype):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1702_00844_gb300.shard import channel_range, corner_turn
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    S, C, T, I = 6, 5, 7, 2
+    rng = np.random.default_rng(11)
+    if dtype == "cf32":
+        full = (rng.standard_normal((I, C, S, T, 2)) + 1j * rng.standard_normal((I, C, S, T, 2))).astype(np.complex64)
+    else:
+        full = rng.integers(-127, 128, size=(I, C, S, T, 2, 2)).astype(np.int8)
+    sct = oracle.reorder(full, "cst", "sct")              # every receiver's stream
+    Sr = S // world
+    mine = torch.from_numpy(np.ascontiguousarray(sct[:, rank * Sr:(rank + 1) * Sr]))
+    got = corner_turn(mine, S, C, T, I, dtype, reorder_fn=_np_reorder)
+    lo, hi = channel_range(C, world, rank)
+    np.testing.assert_array_equal(got.numpy(), full[:, lo:hi])
+    # correlating after the turn gives this rank's channels of the whole array
+    ref = oracle.correlate(full.reshape((I * C,) + full.shape[2:]), dtype)
+    mine_vis = oracle.correlate(got.numpy().reshape((I * (hi - lo),) + full.shape[2:]), dtype)
+    ref = ref.reshape((I, C) + ref.shape[1:])[:, lo:hi].reshape(mine_vis.shape)
+    np.testing.assert_array_equal(mine_vis, ref)
+    with open(os.path.join(out_dir, f"ok{rank}"), "w") as f:
+        f.write("ok")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("dtype", ["cf32", "ci8"])
+def test_corner_turn_two_ranks_gloo(tmp_path, dtype):
+    """Section 7's corner turn over two gloo ranks: each rank starts with all
+    channels of half the stations and ends with its channels of all stations,
+    equal to the oracle's layout of the whole array; its correlation equals
+    the single-process correlation of those channels."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_corner_worker, args=(2, port, str(tmp_path), dtype), nprocs=2, join=True,
+                       start_method="spawn")
+    assert (tmp_path / "ok0").exists() and (tmp_path / "ok1").exists()

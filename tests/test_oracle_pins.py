@@ -303,3 +303,38 @@ def test_planted_mistakes_are_caught(mutation):
     ref = X @ X.conj().T
     F = full_matrix(bad[0], S, 2)
     assert not np.allclose(F, ref, rtol=1e-9, atol=1e-9)
+
+
+# ----------------------------------------------------------- sample layouts
+def _place_by_loops(x_cst, layout):
+    """Builds a layout from its definition with plain loops: element
+    (i, c, s, t) of the correlator layout goes to the layout's index tuple."""
+    I, C, S, T = x_cst.shape[:4]
+    shape = {"cst": (C, S, T), "cts": (C, T, S), "sct": (S, C, T)}[layout]
+    out = np.zeros((I,) + shape + x_cst.shape[4:], dtype=x_cst.dtype)
+    for i in range(I):
+        for c in range(C):
+            for s in range(S):
+                for t in range(T):
+                    idx = {"cst": (c, s, t), "cts": (c, t, s), "sct": (s, c, t)}[layout]
+                    out[(i,) + idx] = x_cst[i, c, s, t]
+    return out
+
+
+def test_reorder_matches_placement_by_definition():
+    rng = np.random.default_rng(7)
+    x = rng.integers(-128, 128, size=(2, 3, 5, 4, 2, 2)).astype(np.int8)  # [I][C][S][T][pol][re,im]
+    layouts = ("cst", "cts", "sct")
+    built = {L: _place_by_loops(x, L) for L in layouts}
+    for a in layouts:
+        for b in layouts:
+            np.testing.assert_array_equal(oracle.reorder(built[a], a, b), built[b])
+
+
+def test_reorder_round_trip_and_composition():
+    rng = np.random.default_rng(8)
+    x = (rng.standard_normal((1, 4, 6, 7, 2)) + 1j * rng.standard_normal((1, 4, 6, 7, 2))).astype(np.complex64)
+    for a in ("cts", "sct"):
+        np.testing.assert_array_equal(oracle.reorder(oracle.reorder(x, "cst", a), a, "cst"), x)
+    np.testing.assert_array_equal(oracle.reorder(oracle.reorder(x, "cst", "sct"), "sct", "cts"),
+                                  oracle.reorder(x, "cst", "cts"))
