@@ -34,7 +34,11 @@
  * waiting on an internal pipeline barrier sets the plan's error word, which
  * corr_get_error reports as CORR_ERR_TIMEOUT.
  *
- * Only two polarisations are supported (n_pols must be 2, as in the paper).
+ * The number of polarisations P is 2 (X and Y, as in the paper) or 1; the
+ * loop nest of Fig. 2 takes it as a parameter. With P = 1 the pol axes have
+ * length 1: the input is [integration][channel][station][time] and the
+ * output [integration][channel][baseline], one complex value per baseline.
+ * Gain calibration and corr_reorder take P = 2 only.
  */
 #ifndef CORR_H
 #define CORR_H
@@ -73,7 +77,7 @@ typedef enum { CORR_PATH_AUTO = 0, CORR_PATH_FP32 = 1, CORR_PATH_TENSOR = 2 } co
 
 typedef struct {
     int n_stations;     /* S >= 1                                   (Section 2) */
-    int n_pols;         /* must be 2 (X and Y)                      (Section 2) */
+    int n_pols;         /* 2 (X and Y) or 1                  (Section 2, Fig. 2) */
     int n_channels;     /* C >= 1                                   (Section 2) */
     int n_samples;      /* T >= 0, samples per integration          (Section 2) */
     int n_integrations; /* >= 1, integrations stacked before channels           */

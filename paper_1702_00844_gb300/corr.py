@@ -143,9 +143,9 @@ def n_baselines(S: int) -> int:
     return S * (S + 1) // 2
 
 
-def input_shape(S: int, C: int, T: int, I: int, dtype: str):
-    """Device tensor shape for samples [I][C][S][T][2 pols] of a dtype."""
-    base = (I, C, S, T, 2)
+def input_shape(S: int, C: int, T: int, I: int, dtype: str, n_pols: int = 2):
+    """Device tensor shape for samples [I][C][S][T][P pols] of a dtype."""
+    base = (I, C, S, T, n_pols)
     return base if dtype == "cf32" else base + (2,)
 
 
@@ -158,11 +158,12 @@ class Plan:
     per integration and I integrations of samples of type ``dtype``."""
 
     def __init__(self, n_stations: int, n_channels: int, n_samples: int, n_integrations: int = 1,
-                 dtype: str = "cf32", path: str = "auto", flags: int = 0):
+                 dtype: str = "cf32", path: str = "auto", flags: int = 0, n_pols: int = 2):
         self.L = lib()
         self.S, self.C, self.T, self.I = n_stations, n_channels, n_samples, n_integrations
         self.dtype = dtype
-        d = Desc(n_stations, 2, n_channels, n_samples, n_integrations, DTYPES[dtype],
+        self.P = n_pols
+        d = Desc(n_stations, n_pols, n_channels, n_samples, n_integrations, DTYPES[dtype],
                  PATHS[path], flags)
         h = ctypes.c_void_p()
         _check(self.L.corr_create(ctypes.byref(d), ctypes.byref(h)), "corr_create")
@@ -170,7 +171,7 @@ class Plan:
 
     # ------------------------------------------------------------- forward
     def out_shape(self):
-        return (self.I, self.C, n_baselines(self.S), 2, 2)
+        return (self.I, self.C, n_baselines(self.S), self.P, self.P)
 
     def empty_out(self, device="cuda"):
         if self.dtype == "ci8":
@@ -181,7 +182,7 @@ class Plan:
         """Visibilities of samples ``x`` (``corr_correlate``)."""
         if out is None:
             out = self.empty_out(x.device)
-        want = self.I * self.C * self.S * self.T * 2 * (1 if self.dtype == "cf32" else 2)
+        want = self.I * self.C * self.S * self.T * self.P * (1 if self.dtype == "cf32" else 2)
         if x.numel() != want or x.dtype != torch_dtype(self.dtype):
             raise ValueError(f"samples: expected {want} elements of {torch_dtype(self.dtype)}")
         _check(self.L.corr_correlate(self.h, _ptr(x), _ptr(out), _stream_handle(stream)),

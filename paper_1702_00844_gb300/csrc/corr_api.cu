@@ -130,6 +130,19 @@ void fp32_config(corr_plan *h)
     h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;
 }
 
+// Bytes of one station-time sample of all npol pols.
+int sample_bytes(int dtype, int npol) { return npol * (dtype == CORR_CF32 ? 8 : dtype == CORR_CF16 ? 4 : 2); }
+
+size_t in_unit_bytes(const corr_desc_t &d)
+{
+    return (size_t)d.n_stations * d.n_samples * sample_bytes(d.dtype, d.n_pols);
+}
+
+size_t out_unit_bytes(const corr_desc_t &d)
+{
+    return (size_t)n_baselines(d.n_stations) * d.n_pols * d.n_pols * 8;
+}
+
 // Work items of the tensor kernel: {prob, unit, rb, cb0 | ncb << 16}, row
 // block rb and column blocks cb0..cb0+ncb-1 of 64 stations, rb <= cb0.
 // narrow: every (rb, cb) with rb <= cb; wide: column blocks taken in pairs
@@ -160,7 +173,12 @@ std::vector<int4> tc_items_for(int prob, int S, int units, int variant)
 
 int bytes_per_sample(int dtype) { return dtype == CORR_CF32 ? 16 : dtype == CORR_CF16 ? 8 : 4; }
 
-TcProblem make_problem(const void *in, void *out, int S, int T, int units, int dtype)
+
+// Stations of the tensor path's work list: with one pol, pairs of stations
+// act as the two pols of one pseudo-station.
+int item_stations(int S, int npol) { return npol == 1 ? (S + 1) / 2 : S; }
+
+TcProblem make_problem(const void *in, void *out, int S, int T, int units, int dtype, int npol)
 {
     TcProblem pr{};
     pr.in = in;
@@ -168,9 +186,9 @@ TcProblem make_problem(const void *in, void *out, int S, int T, int units, int d
     pr.S = S;
     pr.T = T;
     pr.n_units = units;
-    pr.in_unit_bytes = (long long)S * T * bytes_per_sample(dtype);
-    pr.out_unit_elems = n_baselines(S) * 4;
-    pr.vec = (((long long)T * bytes_per_sample(dtype)) % 16 == 0) ? 1 : 0;
+    pr.in_unit_bytes = (long long)S * T * sample_bytes(dtype, npol);
+    pr.out_unit_elems = n_baselines(S) * npol * npol;
+    pr.vec = (((long long)T * sample_bytes(dtype, npol)) % 16 == 0) ? 1 : 0;
     return pr;
 }
 
@@ -222,7 +240,7 @@ corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, int variant, int m
     const bool checked = dtype == CORR_CI8 && max_T > TC_INT8_CHUNK_KB * TC_KB_T && h->redo_cap >= p.n_items;
     if (!checked) {
         p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
-        return cuda_status(tc_launch(dtype, variant, p, grid, s));
+        return cuda_status(tc_launch(dtype, variant, h->d.n_pols, p, grid, s));
     }
     corr_status_t st = cuda_status(cudaMemsetAsync(h->d_redo_mark, 0, (size_t)p.n_items * sizeof(int), s));
     if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count, 0, sizeof(int), s));
@@ -233,7 +251,7 @@ corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, int variant, int m
     a.redo_mark = h->d_redo_mark;
     a.redo_items = h->d_redo_items;
     a.redo_count = h->d_redo_count;
-    st = cuda_status(tc_launch(dtype, variant, a, grid, s));
+    st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
     if (st != CORR_OK) return st;
     TcParams b = p;
     b.items = h->d_redo_items;
@@ -241,14 +259,14 @@ corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, int variant, int m
     b.n_items_dev = h->d_redo_count;
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
-    return cuda_status(tc_launch(dtype, variant, b, tc_grid_for(h, variant, p.n_items), s));
+    return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s));
 }
 
 corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long long units,
                            cudaStream_t s)
 {
     const corr_desc_t &d = h->d;
-    const size_t out_bytes = (size_t)(units * n_baselines(d.n_stations) * 4 * 8);
+    const size_t out_bytes = (size_t)units * out_unit_bytes(d);
     if (d.n_samples == 0) return cuda_status(cudaMemsetAsync(d_out, 0, out_bytes, s));
     if (h->path == CORR_PATH_FP32) {
         CUtensorMap m;
@@ -262,7 +280,7 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
         return cuda_status(fp32_launch(&m, p, h->fp_threads, h->fp_smem, s));
     }
     TcParams p{};
-    p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype);
+    p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype, d.n_pols);
     p.probs = nullptr;
     p.items = h->d_items; // unit-major, so the first units' items are a prefix
     p.n_items = (int)((long long)h->n_items / ((long long)d.n_channels * d.n_integrations) * units);
@@ -276,12 +294,6 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
     return launch_units(h, d_in, d_out, (long long)h->d.n_channels * h->d.n_integrations, s);
 }
 
-size_t in_unit_bytes(const corr_desc_t &d)
-{
-    return (size_t)d.n_stations * d.n_samples * bytes_per_sample(d.dtype);
-}
-
-size_t out_unit_bytes(const corr_desc_t &d) { return (size_t)n_baselines(d.n_stations) * 4 * 8; }
 
 // ------------------------------------------------------------------ autotuner
 // The tile variant of the tensor path is chosen per (device, dtype, S, T) by
@@ -290,10 +302,10 @@ size_t out_unit_bytes(const corr_desc_t &d) { return (size_t)n_baselines(d.n_sta
 // narrow|wide|pair forces one or CORR_FLAG_NO_AUTOTUNE asks for the
 // heuristic (pair from 128 stations). Choices are cached for the process.
 struct TuneKey {
-    int dev, dtype, S, T;
+    int dev, dtype, npol, S, T;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(dev, dtype, S, T) < std::tie(o.dev, o.dtype, o.S, o.T);
+        return std::tie(dev, dtype, npol, S, T) < std::tie(o.dev, o.dtype, o.npol, o.S, o.T);
     }
 };
 std::mutex g_tune_mu;
@@ -312,7 +324,7 @@ int forced_variant()
 corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, const void *d_in,
                            void *d_out, float *ms_out)
 {
-    std::vector<int4> items = tc_items_for(0, S, units, variant);
+    std::vector<int4> items = tc_items_for(0, item_stations(S, h->d.n_pols), units, variant);
     int4 *d_items = nullptr;
     corr_status_t st = cuda_status(cudaMalloc(&d_items, items.size() * sizeof(int4)));
     if (st != CORR_OK) return st;
@@ -322,7 +334,7 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
                                          cudaMemcpyHostToDevice))) != CORR_OK)
             break;
         TcParams p{};
-        p.prob0 = make_problem(d_in, d_out, S, T, units, h->d.dtype);
+        p.prob0 = make_problem(d_in, d_out, S, T, units, h->d.dtype, h->d.n_pols);
         p.items = d_items;
         p.n_items = (int)items.size();
         p.err = h->d_err;
@@ -361,7 +373,7 @@ corr_status_t tune_tensor_variant(corr_plan *h)
         h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
         return CORR_OK;
     }
-    const TuneKey key{h->device, d.dtype, d.n_stations, d.n_samples};
+    const TuneKey key{h->device, d.dtype, d.n_pols, d.n_stations, d.n_samples};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -371,10 +383,11 @@ corr_status_t tune_tensor_variant(corr_plan *h)
         }
     }
     const long long units = (long long)d.n_channels * d.n_integrations;
-    const long long per_unit = (long long)tc_blocks(d.n_stations) * (tc_blocks(d.n_stations) + 1) / 2;
+    const int nbu = tc_blocks(item_stations(d.n_stations, d.n_pols));
+    const long long per_unit = (long long)nbu * (nbu + 1) / 2;
     const int su = (int)std::max(1LL, std::min(units, (4LL * h->sm_count + per_unit - 1) / per_unit));
-    const size_t in_bytes = (size_t)su * d.n_stations * d.n_samples * bytes_per_sample(d.dtype);
-    const size_t out_bytes = (size_t)su * n_baselines(d.n_stations) * 4 * 8;
+    const size_t in_bytes = (size_t)su * in_unit_bytes(d);
+    const size_t out_bytes = (size_t)su * out_unit_bytes(d);
     void *d_in = nullptr, *d_out = nullptr;
     corr_status_t st = cuda_status(cudaMalloc(&d_in, in_bytes));
     if (st == CORR_OK) st = cuda_status(cudaMalloc(&d_out, out_bytes));
@@ -480,17 +493,18 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
     const corr_desc_t &d = *desc;
     if (d.n_stations < 1 || d.n_channels < 1 || d.n_samples < 0 || d.n_integrations < 1)
         return CORR_ERR_INVALID_ARG;
-    if (d.n_pols != 2) return CORR_ERR_UNSUPPORTED;
+    if (d.n_pols != 1 && d.n_pols != 2) return CORR_ERR_UNSUPPORTED;
     if (d.dtype < CORR_CF32 || d.dtype > CORR_CI8) return CORR_ERR_INVALID_ARG;
     if (d.path < CORR_PATH_AUTO || d.path > CORR_PATH_TENSOR) return CORR_ERR_INVALID_ARG;
     int path = d.path;
     if (path == CORR_PATH_AUTO) path = d.dtype == CORR_CF32 ? CORR_PATH_FP32 : CORR_PATH_TENSOR;
     if (path == CORR_PATH_FP32 && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
     if (path == CORR_PATH_TENSOR && d.dtype == CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    if (path == CORR_PATH_FP32 && d.n_pols == 1) return CORR_ERR_UNSUPPORTED;
     if (d.dtype == CORR_CI8 && d.n_samples > 65535) return CORR_ERR_UNSUPPORTED; // int32 range
     const long long units = (long long)d.n_channels * d.n_integrations;
     if (units > (1LL << 30) || d.n_stations > 65535) return CORR_ERR_UNSUPPORTED;
-    if ((d.flags & CORR_FLAG_GAINS) && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    if ((d.flags & CORR_FLAG_GAINS) && (d.dtype != CORR_CF32 || d.n_pols != 2)) return CORR_ERR_UNSUPPORTED;
 
     corr_plan *h = new (std::nothrow) corr_plan();
     if (!h) return CORR_ERR_NO_MEMORY;
@@ -519,7 +533,8 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             fp32_config(h);
         } else {
             if ((st = tune_tensor_variant(h)) != CORR_OK) break;
-            std::vector<int4> items = tc_items_for(0, d.n_stations, (int)units, h->tc_variant);
+            std::vector<int4> items =
+                tc_items_for(0, item_stations(d.n_stations, d.n_pols), (int)units, h->tc_variant);
             h->n_items = (int)items.size();
             if ((st = cuda_status(cudaMalloc(&h->d_items, items.size() * sizeof(int4)))) != CORR_OK)
                 break;
@@ -657,9 +672,10 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
         for (int i = 0; i < n_sub; ++i) {
             const corr_subarray_t &s = subs[i];
             probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
-                                         h->d.dtype));
+                                         h->d.dtype, h->d.n_pols));
             if (s.n_samples == 0) continue;
-            std::vector<int4> v = tc_items_for(i, s.n_stations, s.n_channels, h->b_variant);
+            std::vector<int4> v =
+                tc_items_for(i, item_stations(s.n_stations, h->d.n_pols), s.n_channels, h->b_variant);
             items.insert(items.end(), v.begin(), v.end());
         }
         std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
@@ -687,7 +703,8 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     }
     for (int i = 0; i < n_sub; ++i)
         if (subs[i].n_samples == 0) {
-            const size_t bytes = (size_t)subs[i].n_channels * n_baselines(subs[i].n_stations) * 4 * 8;
+            const size_t bytes = (size_t)subs[i].n_channels * n_baselines(subs[i].n_stations) *
+                                 h->d.n_pols * h->d.n_pols * 8;
             corr_status_t e = cuda_status(cudaMemsetAsync(subs[i].d_out, 0, bytes, st));
             if (e != CORR_OK) return e;
         }

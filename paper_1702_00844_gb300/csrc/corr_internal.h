@@ -9,10 +9,10 @@ namespace corr {
 // One correlation problem for the tcgen05 kernel: n_units independent
 // channels (integrations x channels) of S stations and T samples.
 struct TcProblem {
-    const void *in;           // [unit][S][T][2 pols] complex f16 or int8
-    void *out;                // [unit][S(S+1)/2][2][2] complex f32 or int32
-    long long in_unit_bytes;  // S*T*2*sizeof(complex sample)
-    long long out_unit_elems; // S(S+1)/2 * 4 complex values
+    const void *in;           // [unit][S][T][P pols] complex f16 or int8
+    void *out;                // [unit][S(S+1)/2][P][P] complex f32 or int32
+    long long in_unit_bytes;  // S*T*P*sizeof(complex sample)
+    long long out_unit_elems; // S(S+1)/2 * P*P complex values
     int S, T, n_units, vec;   // vec: 16-byte vector loads are aligned
 };
 
@@ -47,8 +47,9 @@ constexpr int TC_KB_T = 32;    // time samples per K-block
 constexpr int TC_THREADS = 13 * 32;
 constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 
-// grid: CTAs (even for TC_PAIR: two per cluster).
-cudaError_t tc_launch(int dtype, int variant, const TcParams &p, int grid, cudaStream_t s);
+// grid: CTAs (even for TC_PAIR: two per cluster). npol: 1 or 2 polarisations
+// (with 1, the items are over pseudo-stations of two stations each).
+cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s);
 // Clusters of the pair variant that fit on the device at once.
 cudaError_t tc_pair_max_clusters(int dtype, int *n);
 

@@ -155,10 +155,51 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
 // pair the same samples. Samples outside [0,S) x [0,T) are zero-filled. With
 // vec (rows of whole 16-byte chunks) 16-byte copies are used, otherwise one
 // copy per sample.
-template <int DT>
+template <int DT, int NPOL>
 __device__ __forceinline__ void issue_raw(const uint8_t *unit_in, int S, int T, bool vec, int s,
                                           int t0, int g, uint32_t dst, uint32_t chunk_stride)
 {
+    if constexpr (NPOL == 1) {
+        // Single polarisation: s is a pseudo-station, stations 2s and 2s+1
+        // play its two pols. Chunk q = (station parity p, half h): samples
+        // t0 + 8g + 4h*(DT == 1) .. of station 2s + p, 16 bytes each.
+        constexpr int BPS = DT == 1 ? 4 : 2;  // bytes per sample of one station
+        constexpr int HALVES = DT == 1 ? 2 : 1;
+        constexpr int TPC = 16 / BPS;         // samples per chunk
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int st = 2 * s + p;
+            const bool srow = st < S;
+            const uint8_t *row = unit_in + (srow ? (size_t)st * T * BPS : 0);
+#pragma unroll
+            for (int h = 0; h < HALVES; ++h) {
+                const uint32_t d = dst + (p * HALVES + h) * chunk_stride;
+                const int tq = t0 + 8 * g + h * TPC;
+                if (vec) {
+                    int nb = srow ? (T - tq) * BPS : 0;
+                    nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+                    cp_async16(d, nb ? row + (size_t)tq * BPS : unit_in, (uint32_t)nb);
+                } else if (BPS == 4) {
+#pragma unroll
+                    for (int i = 0; i < TPC; ++i) {
+                        const uint32_t nb = (srow && tq + i < T) ? 4u : 0u;
+                        cp_async_small<4>(d + i * 4, nb ? row + (size_t)(tq + i) * 4 : unit_in, nb);
+                    }
+                } else {
+                    // 2-byte samples have no asynchronous copy: plain loads
+                    // and shared stores, read back by this thread only
+#pragma unroll
+                    for (int i = 0; i < TPC; ++i) {
+                        const unsigned short v = (srow && tq + i < T)
+                            ? *reinterpret_cast<const unsigned short *>(row + (size_t)(tq + i) * 2)
+                            : (unsigned short)0;
+                        asm volatile("st.shared.u16 [%0], %1;" ::"r"(d + i * 2), "h"(v) : "memory");
+                    }
+                }
+            }
+        }
+        return;
+    }
     constexpr int BPT = DT == 1 ? 8 : 4;     // bytes per time sample (2 pols, re+im)
     constexpr int NQ = RawBytes<DT>::value / 16;
     constexpr int TPQ = 16 / BPT;            // samples per 16-byte chunk
@@ -210,11 +251,32 @@ __device__ __forceinline__ uint32_t i8pair_to_h2(uint32_t u)
 
 // Splits 8 samples of one station into 4 chunks of 8 f16 each:
 // re[p] = real parts of pol p, im[p] = imaginary parts of pol p.
-template <int DT>
+template <int DT, int NPOL>
 __device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&im)[2])
 {
     uint32_t o_re[2][4], o_im[2][4];
-    if (DT == 1) {
+    if (NPOL == 1 && DT == 1) {
+        // chunk 2p+h = 4 samples of station 2s+p, word = (re, im) f16
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 &c = r.v[2 * p + (q >> 1)];
+                const uint32_t w0 = word_of(c, 2 * (q & 1)), w1 = word_of(c, 2 * (q & 1) + 1);
+                o_re[p][q] = __byte_perm(w0, w1, 0x5410);
+                o_im[p][q] = __byte_perm(w0, w1, 0x7632);
+            }
+    } else if (NPOL == 1) {
+        // chunk p = 8 samples of station 2s+p, word = bytes (re, im, re, im)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t w = word_of(r.v[p], q);
+                o_re[p][q] = i8pair_to_h2(w);
+                o_im[p][q] = i8pair_to_h2(w >> 8);
+            }
+    } else if (DT == 1) {
         // word 2t+p = (re, im) of pol p at the unit's t-th sample (low half = re)
 #pragma unroll
         for (int p = 0; p < 2; ++p)
@@ -251,11 +313,11 @@ __device__ __forceinline__ void split(const Raw<DT> &r, uint4 (&re)[2], uint4 (&
 // (row = 2*sl + pol; chunk g = real parts, chunk 4+g = imaginary parts) in the
 // 128-byte swizzled layout. The order of the four stores alternates with the
 // station parity so that each quarter-warp hits 8 distinct 16-byte bank groups.
-template <int DT>
+template <int DT, int NPOL>
 __device__ __forceinline__ void store_tile(uint32_t tile, int sl, int g, const Raw<DT> &r)
 {
     uint4 re[2], im[2];
-    split<DT>(r, re, im);
+    split<DT, NPOL>(r, re, im);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int p = k >> 1;
@@ -292,11 +354,39 @@ __device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
 // thread against column stations s2_0 .. s2_0+7 (both p2), masked to
 // s1 <= s2 < S. int8: converts the exact FP32 chunk sums to INT32 and adds
 // the earlier chunks' partial sums (fold).
-template <int DT>
+template <int DT, int NPOL>
 __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_off, int s1, int s2_0,
                                             bool fold, bool last, const uint32_t (&vre)[16],
                                             const uint32_t (&vim)[16])
 {
+    if constexpr (NPOL == 1) {
+        // s1: this row's station; column 2j + p2 is station 2(s2_0 + j) + p2;
+        // one complex per baseline
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int s2 = 2 * s2_0 + k;
+            if (!(s1 <= s2 && s2 < P.S)) continue;
+            const long long e = unit_off + (long long)s2 * (s2 + 1) / 2 + s1;
+            if (DT == 1) {
+                float2 *dst = static_cast<float2 *>(P.out) + e;
+                __stcs(dst, make_float2(__uint_as_float(vre[k]), __uint_as_float(vim[k])));
+            } else {
+                int2 *dst = static_cast<int2 *>(P.out) + e;
+                int2 v = make_int2(__float2int_rn(__uint_as_float(vre[k])),
+                                   __float2int_rn(__uint_as_float(vim[k])));
+                if (fold) {
+                    const int2 o = __ldcg(dst);
+                    v.x += o.x;
+                    v.y += o.y;
+                }
+                if (last)
+                    __stcs(dst, v);
+                else
+                    __stcg(dst, v);
+            }
+        }
+        return;
+    }
     if (DT == 1) {
         float2 *out = static_cast<float2 *>(P.out) + unit_off;
 #pragma unroll
@@ -342,7 +432,11 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
     }
 }
 
-template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
+// NPOL = 2: rows are (station, pol). NPOL = 1: rows are stations; stations
+// 2m and 2m+1 take the places of the two pols of "pseudo-station" m, so the
+// tiles, the schedule (over pseudo-stations) and the MMAs are those of the
+// two-pol case and only the sample copies and the output mapping differ.
+template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
 {
     using C = Cfg<DT, V>;
     constexpr bool PAIR = V == TC_PAIR;
@@ -445,7 +539,7 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
 #pragma unroll
                     for (int j = 0; j < NSLOT; ++j)
                         if (j <= nB)
-                            issue_raw<DT>(unit_in, P.S, P.T, vec, st_of[j], k * TC_KB_T, g,
+                            issue_raw<DT, NPOL>(unit_in, P.S, P.T, vec, st_of[j], k * TC_KB_T, g,
                                           slot_addr(k, j), CHUNK);
                 }
                 cp_async_commit(); // one group per K-block (empty past the end)
@@ -469,7 +563,7 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                 const uint32_t st = tiles_u32 + stage * STAGE;
 #pragma unroll
                 for (int j = 0; j < NSLOT; ++j)
-                    if (j <= nB) store_tile<DT>(st + j * TILE_BYTES, sl, g, r[j]);
+                    if (j <= nB) store_tile<DT, NPOL>(st + j * TILE_BYTES, sl, g, r[j]);
                 if (check) {
 #pragma unroll
                     for (int j = 0; j < NSLOT; ++j)
@@ -525,9 +619,11 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
             const TcProblem P = get_prob(p, item.prob);
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const int nch = n_chunks(nkb, p.chunk_kb);
-            const int s1 = (item.rb + (int)rank) * TC_RS + sl;
-            const int ngroups = 8 * item.ncb;  // groups of 8 column stations
-            const long long unit_off = (long long)item.unit * P.out_unit_elems + p1 * 2;
+            // NPOL = 1: the row's station; NPOL = 2: its station (pol p1)
+            const int s1 = NPOL == 1 ? (item.rb + (int)rank) * 2 * TC_RS + row
+                                     : (item.rb + (int)rank) * TC_RS + sl;
+            const int ngroups = 8 * item.ncb;  // groups of 8 column (pseudo-)stations
+            const long long unit_off = (long long)item.unit * P.out_unit_elems + (NPOL == 1 ? 0 : p1 * 2);
             for (int c = 0; c < nch; ++c, ++acc_it) {
                 const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
                 if (!mbar_wait_bounded(&bars->acc_full[buf], ap, abort_flag, p.err, p.wait_ns)) {
@@ -554,7 +650,7 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                         tmem_ld_32x32b_x16(taddr + (cc + 1) * 16, rb2);
                         tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 1) * 16, ib2);
                     }
-                    store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
+                    store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
                     tmem_wait_ld();
                     if (cc + 2 >= ngroups) {  // every column of this chunk has been read
                         tc_fence_before();
@@ -566,7 +662,7 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
                             tmem_ld_32x32b_x16(taddr + (cc + 2) * 16, ra);
                             tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 2) * 16, ia);
                         }
-                        store_group<DT>(P, unit_off, s1, item.cb0 * TC_RS + (cc + 1) * 8, c > 0, last,
+                        store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + (cc + 1) * 8, c > 0, last,
                                         rb2, ib2);
                         if (cc + 2 < ngroups) tmem_wait_ld();
                     }
@@ -723,68 +819,70 @@ template <int DT, int V> __device__ __forceinline__ void tc_correlate_body(const
     }
 }
 
-template <int DT, int V>
+template <int DT, int V, int NPOL>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __grid_constant__ TcParams p)
 {
-    tc_correlate_body<DT, V>(p);
+    tc_correlate_body<DT, V, NPOL>(p);
 }
 
-template <int DT>
+template <int DT, int NPOL>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     tc_pair_kernel(const __grid_constant__ TcParams p)
 {
-    tc_correlate_body<DT, TC_PAIR>(p);
+    tc_correlate_body<DT, TC_PAIR, NPOL>(p);
 }
 
-template <int DT, int V> const void *kernel_ptr()
+template <int DT, int V, int NPOL> const void *kernel_ptr()
 {
     if constexpr (V == TC_PAIR)
-        return reinterpret_cast<const void *>(&tc_pair_kernel<DT>);
+        return reinterpret_cast<const void *>(&tc_pair_kernel<DT, NPOL>);
     else
-        return reinterpret_cast<const void *>(&tc_correlate_kernel<DT, V>);
+        return reinterpret_cast<const void *>(&tc_correlate_kernel<DT, V, NPOL>);
 }
 
 template <int DT, int V> size_t smem_total() { return (size_t)smem_bytes<DT, V>() + sizeof(Bars) + 1024; }
 
-template <int DT, int V> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
+template <int DT, int V, int NPOL> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
 {
     const size_t smem = smem_total<DT, V>();
-    cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V>(),
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V, NPOL>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if constexpr (V == TC_PAIR)
-        tc_pair_kernel<DT><<<grid, TC_THREADS, smem, s>>>(p);
+        tc_pair_kernel<DT, NPOL><<<grid, TC_THREADS, smem, s>>>(p);
     else
-        tc_correlate_kernel<DT, V><<<grid, TC_THREADS, smem, s>>>(p);
+        tc_correlate_kernel<DT, V, NPOL><<<grid, TC_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int DT> cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s)
+template <int DT, int NPOL> cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s)
 {
-    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR>(p, grid, s);
-    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE>(p, grid, s);
-    return launch_one<DT, TC_NARROW>(p, grid, s);
+    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR, NPOL>(p, grid, s);
+    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE, NPOL>(p, grid, s);
+    return launch_one<DT, TC_NARROW, NPOL>(p, grid, s);
 }
 
 template <int DT> cudaError_t pair_clusters_dt(int *n)
 {
     const size_t smem = smem_total<DT, TC_PAIR>();
-    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT>,
+    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT, 2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, 1, 1);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    return cudaOccupancyMaxActiveClusters(n, tc_pair_kernel<DT>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, tc_pair_kernel<DT, 2>, &cfg);
 }
 
 } // namespace
 
-cudaError_t tc_launch(int dtype, int variant, const TcParams &p, int grid, cudaStream_t s)
+cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s)
 {
     if (variant == TC_PAIR && (grid < 2 || grid % 2 != 0)) return cudaErrorInvalidValue;
-    return dtype == 1 ? launch_dt<1>(variant, p, grid, s) : launch_dt<2>(variant, p, grid, s);
+    if (npol == 1)
+        return dtype == 1 ? launch_dt<1, 1>(variant, p, grid, s) : launch_dt<2, 1>(variant, p, grid, s);
+    return dtype == 1 ? launch_dt<1, 2>(variant, p, grid, s) : launch_dt<2, 2>(variant, p, grid, s);
 }
 
 cudaError_t tc_pair_max_clusters(int dtype, int *n)

@@ -338,3 +338,25 @@ def test_reorder_round_trip_and_composition():
         np.testing.assert_array_equal(oracle.reorder(oracle.reorder(x, "cst", a), a, "cst"), x)
     np.testing.assert_array_equal(oracle.reorder(oracle.reorder(x, "cst", "sct"), "sct", "cts"),
                                   oracle.reorder(x, "cst", "cts"))
+
+
+# ------------------------------------------------------ single polarisation
+def test_single_pol_is_the_xx_block_of_two_pols():
+    """With P = 1 the loop nest of Fig. 2 runs over one pol: its visibilities
+    equal the XX entries of a P = 2 correlation whose X pol carries the same
+    samples (whatever Y holds), and a brute-force sum of exact integers."""
+    rng = np.random.default_rng(21)
+    C, S, T = 3, 7, 19
+    x1 = rng.integers(-128, 128, size=(C, S, T, 1, 2)).astype(np.int8)
+    y = rng.integers(-128, 128, size=(C, S, T, 1, 2)).astype(np.int8)
+    x2 = np.concatenate([x1, y], axis=3)                       # pols (X = x1, Y = other)
+    v1 = oracle.correlate(x1, "ci8")
+    v2 = oracle.correlate(x2, "ci8")
+    assert v1.shape == (C, S * (S + 1) // 2, 1, 1)
+    np.testing.assert_array_equal(v1[..., 0, 0], v2[..., 0, 0])
+    z = x1[..., 0, 0].astype(np.int64) + 1j * x1[..., 0, 1].astype(np.int64)
+    for c in range(C):
+        for s2 in range(S):
+            for s1 in range(s2 + 1):
+                want = sum(complex(z[c, s1, t]) * complex(z[c, s2, t]).conjugate() for t in range(T))
+                assert v1[c, s2 * (s2 + 1) // 2 + s1, 0, 0] == want
