@@ -300,6 +300,17 @@ def secondary(x8, torch):
     res["gain_forward_backward_differentiation"] = {"ms": ms}
     del pg, xd, gd, Md, R, gg, gx
     torch.cuda.empty_cache()
+    # one polarisation: the int8 samples read as 512 stations of one pol (the
+    # same bytes, and the same products per channel as 256 two-pol stations)
+    p1 = Plan(2 * S3, C3, T3, dtype="ci8", path="tensor", n_pols=1)
+    x1 = x8.view(C3, 2 * S3, T3, 1, 2)
+    o1 = p1.empty_out()
+    ms = time_launches(lambda: p1.correlate(x1, o1), 10, 3, st)
+    ops1 = 8.0 * (2 * S3) * (2 * S3 + 1) / 2 * T3 * C3
+    res["tensor_int8_single_pol_512_stations"] = {"ms": ms, "TOPS": ops1 / ms / 1e9,
+                                                  "variant": p1.tile_variant()}
+    del p1, o1
+    torch.cuda.empty_cache()
     # sample layouts (corr_reorder) on the int8 precision samples: the
     # time-major layout of Section 4.4 and the per-station streams before the
     # corner turn of Section 7, each into the correlator's layout. HBM-bound:

@@ -110,11 +110,17 @@ corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, in
     return CORR_OK;
 }
 
+// Stations of the work lists and sub-tile grids: with one pol, pairs of stations
+// act as the two pols of one pseudo-station.
+int item_stations(int S, int npol) { return npol == 1 ? (S + 1) / 2 : S; }
+
 void fp32_config(corr_plan *h)
 {
-    const int S = h->d.n_stations;
+    // one pol: sub-tiles over pseudo-stations (pairs of stations)
+    const int S = item_stations(h->d.n_stations, h->d.n_pols);
     Fp32Params &p = h->fp;
     p.S = S;
+    p.S1 = h->d.n_stations;
     p.T = h->d.n_samples;
     p.n_units = h->d.n_channels * h->d.n_integrations;
     p.nq = (S + 3) / 4;
@@ -174,9 +180,6 @@ std::vector<int4> tc_items_for(int prob, int S, int units, int variant)
 int bytes_per_sample(int dtype) { return dtype == CORR_CF32 ? 16 : dtype == CORR_CF16 ? 8 : 4; }
 
 
-// Stations of the tensor path's work list: with one pol, pairs of stations
-// act as the two pols of one pseudo-station.
-int item_stations(int S, int npol) { return npol == 1 ? (S + 1) / 2 : S; }
 
 TcProblem make_problem(const void *in, void *out, int S, int T, int units, int dtype, int npol)
 {
@@ -269,15 +272,18 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     const size_t out_bytes = (size_t)units * out_unit_bytes(d);
     if (d.n_samples == 0) return cuda_status(cudaMemsetAsync(d_out, 0, out_bytes, s));
     if (h->path == CORR_PATH_FP32) {
-        CUtensorMap m;
-        corr_status_t st = encode_fp32_map(&m, d_in, d.n_stations, d.n_samples, (int)units, h->fp.tc);
-        if (st != CORR_OK) return st;
+        CUtensorMap m{};
+        if (d.n_pols == 2) {
+            corr_status_t st = encode_fp32_map(&m, d_in, d.n_stations, d.n_samples, (int)units, h->fp.tc);
+            if (st != CORR_OK) return st;
+        }
         Fp32Params p = h->fp;
         p.n_units = (int)units;
         p.out = static_cast<float2 *>(d_out);
+        p.in1 = static_cast<const float2 *>(d_in);
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
-        return cuda_status(fp32_launch(&m, p, h->fp_threads, h->fp_smem, s));
+        return cuda_status(fp32_launch(&m, p, d.n_pols, h->fp_threads, h->fp_smem, s));
     }
     TcParams p{};
     p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype, d.n_pols);
@@ -500,7 +506,6 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
     if (path == CORR_PATH_AUTO) path = d.dtype == CORR_CF32 ? CORR_PATH_FP32 : CORR_PATH_TENSOR;
     if (path == CORR_PATH_FP32 && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
     if (path == CORR_PATH_TENSOR && d.dtype == CORR_CF32) return CORR_ERR_UNSUPPORTED;
-    if (path == CORR_PATH_FP32 && d.n_pols == 1) return CORR_ERR_UNSUPPORTED;
     if (d.dtype == CORR_CI8 && d.n_samples > 65535) return CORR_ERR_UNSUPPORTED; // int32 range
     const long long units = (long long)d.n_channels * d.n_integrations;
     if (units > (1LL << 30) || d.n_stations > 65535) return CORR_ERR_UNSUPPORTED;

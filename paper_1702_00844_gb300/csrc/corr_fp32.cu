@@ -13,6 +13,13 @@
 // Registers are capped at 168 per thread and CTAs at 192 threads so that two
 // CTAs share an SM (at most 3 warps per SM sub-partition).
 //
+// One polarisation (NPOL = 1): stations 2m and 2m+1 act as the two pols of
+// pseudo-station m. A box of 16 stations x tc samples of 8-byte complex
+// values, stored time-major, is byte for byte a box of 8 pseudo-stations of
+// 16-byte two-pol samples, so the arithmetic is unchanged. Those boxes are
+// staged with 8-byte asynchronous copies by all threads (a TMA box needs an
+// innermost extent of 16 bytes), and only the output mapping differs.
+//
 // Samples are staged by TMA: each stage holds `tc` samples of every station
 // the CTA needs, as boxes of 8 stations stored time-major
 // ([box][t][8 stations][2 pols x complex]). Thread j reads its four column
@@ -49,6 +56,30 @@ __device__ __noinline__ void drain_issued(uint64_t *full, int kc, int nchunks, i
         mbar_wait_bounded(&full[c % FP32_STAGES], (c / FP32_STAGES) & 1, &dummy, err, 2000000000ull);
 }
 
+// One polarisation: copies chunk kc (tc samples) of stations 2*s_lo ..
+// 2*s_lo + 16*nbox - 1 into the stage at shared address `base`, laid out
+// [box][t][16 stations][8 bytes]; this thread takes elements tid, tid +
+// nthreads, ... (time fastest); zero fill outside the array. Ends one
+// commit group (empty past the last chunk). Kept out of line so that its
+// registers do not compete with the accumulators.
+__device__ __noinline__ void stage_single_pol(uint32_t base, const float2 *in1u, const float2 *any,
+                                              int S1, int T, int tc, int s_lo, int nbox, int kc,
+                                              int nchunks, int tid, int nthreads)
+{
+    if (kc < nchunks) {
+        const int n = nbox * 16 * tc;
+        for (int e = tid; e < n; e += nthreads) {
+            const int tl = e % tc, sl16 = e / tc; // station offset from 2 * s_lo
+            const int s = 2 * s_lo + sl16, t = kc * tc + tl;
+            const uint32_t dst = base + (uint32_t)(((sl16 >> 4) * tc + tl) * 16 + (sl16 & 15)) * 8u;
+            const bool in = s < S1 && t < T;
+            cp_async_small<8>(dst, in ? in1u + (size_t)s * T + t : any, in ? 8u : 0u);
+        }
+    }
+    cp_async_commit();
+}
+
+template <int NPOL>
 __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const Fp32Params p)
 {
@@ -76,7 +107,7 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     const int nchunks = (p.T + p.tc - 1) / p.tc;
 
     if (tid == 0) {
-        prefetch_tmap(&tmap);
+        if (NPOL == 2) prefetch_tmap(&tmap);
         for (int s = 0; s < FP32_STAGES; ++s) mbar_init(&full[s], 1);
         abort_flag = 0;
         fence_mbar_init();
@@ -90,8 +121,19 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
             tma_load_4d(smem + (size_t)st * stage_bytes + (size_t)b * box_f4 * 16, &tmap, &full[st],
                         0, s_lo + 8 * b, kc * p.tc, unit);
     };
-    if (tid == 0)
+    // NPOL = 1: every thread copies its share of the stage's (station, time)
+    // values (time fastest, so a warp reads contiguous samples of a station);
+    // one commit group per stage, zero fill outside the array.
+    auto issue1 = [&](int kc) {
+        stage_single_pol(smem_u32(smem) + (uint32_t)(kc % FP32_STAGES) * stage_bytes,
+                         p.in1 + (size_t)unit * p.S1 * p.T, p.in1, p.S1, p.T, p.tc, s_lo, nbox, kc,
+                         nchunks, tid, (int)blockDim.x);
+    };
+    if (NPOL == 1) {
+        for (int kc = 0; kc < FP32_STAGES; ++kc) issue1(kc);
+    } else if (tid == 0) {
         for (int kc = 0; kc < FP32_STAGES && kc < nchunks; ++kc) issue(kc);
+    }
 
     int row_off[4], col_off[4];
 #pragma unroll
@@ -113,8 +155,13 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     const float4 *sm4 = reinterpret_cast<const float4 *>(smem);
     for (int kc = 0; kc < nchunks; ++kc) {
         const int st = kc % FP32_STAGES;
-        const bool ok = mbar_wait_bounded(&full[st], (kc / FP32_STAGES) & 1, &abort_flag, p.err,
-                                          p.wait_ns);
+        bool ok = true;
+        if (NPOL == 1) {
+            cp_async_wait<FP32_STAGES - 1>(); // this thread's copies of chunk kc
+            __syncthreads();                  // everyone's
+        } else {
+            ok = mbar_wait_bounded(&full[st], (kc / FP32_STAGES) & 1, &abort_flag, p.err, p.wait_ns);
+        }
         if (ok) {
             const float4 *base = sm4 + (size_t)st * stage_f4;
             const int tn = min(p.tc, p.T - kc * p.tc);
@@ -143,6 +190,10 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
             }
         }
         __syncthreads();
+        if (NPOL == 1) {
+            issue1(kc + FP32_STAGES);
+            continue;
+        }
         if (abort_flag) {
             // Let every issued TMA load land before the CTA (and its shared
             // memory) goes away; fixed 2 s bound per stage.
@@ -151,8 +202,29 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         }
         if (tid == 0 && kc + FP32_STAGES < nchunks) issue(kc + FP32_STAGES);
     }
+    if (NPOL == 1) cp_async_wait<0>();
 
     if (!active || abort_flag) return;
+    if (NPOL == 1) {
+        // pseudo rows 4i+a (stations 2(4i+a)+p1) x pseudo columns (stations
+        // 2 col + p2); one complex per baseline
+        const long long B1 = (long long)p.S1 * (p.S1 + 1) / 2;
+        float2 *out = p.out + (long long)unit * B1;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int m1 = 4 * i + a, m2 = 4 * j + ((b + (j >> 1)) & 3);
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int s1 = 2 * m1 + (pp >> 1), s2 = 2 * m2 + (pp & 1);
+                    if (s1 <= s2 && s2 < p.S1)
+                        out[(long long)s2 * (s2 + 1) / 2 + s1] =
+                            make_float2(acc[a][b][2 * pp], acc[a][b][2 * pp + 1]);
+                }
+            }
+        return;
+    }
     const long long B = (long long)p.S * (p.S + 1) / 2;
     float2 *out = p.out + (long long)unit * B * 4;
 #pragma unroll
@@ -172,14 +244,22 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
 
 } // namespace
 
-cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int threads, size_t smem,
+cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int threads, size_t smem,
                         cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel,
+    if (npol == 1) {
+        cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        CUtensorMap unused{};
+        fp32_correlate_kernel<1><<<p.n_units * p.groups, threads, smem, s>>>(unused, p);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    fp32_correlate_kernel<<<p.n_units * p.groups, threads, smem, s>>>(*m, p);
+    fp32_correlate_kernel<2><<<p.n_units * p.groups, threads, smem, s>>>(*m, p);
     return cudaGetLastError();
 }
 

@@ -56,14 +56,19 @@ cudaError_t tc_pair_max_clusters(int dtype, int *n);
 // ------------------------------------------------------------------ FP32 path
 struct Fp32Params {
     float2 *out;
-    int S, T, n_units;
+    int S, T, n_units;                // S: (pseudo-)stations of the sub-tile grid
     int nq, nsub, groups, group_size; // 4x4 sub-tiles per unit and grouping
     int tc;                           // samples per pipeline stage
     int *err;
     unsigned long long wait_ns;
+    // one polarisation: the samples [unit][station][time] complex64, and the
+    // real station count (S = ceil(S1 / 2) pseudo-stations)
+    const float2 *in1;
+    int S1;
 };
 constexpr int FP32_STAGES = 3;
-cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int threads, size_t smem,
+// npol 2: samples through the TMA map tmap; npol 1: through p.in1.
+cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int threads, size_t smem,
                         cudaStream_t s);
 
 // -------------------------------------------------------------- gain adjoint

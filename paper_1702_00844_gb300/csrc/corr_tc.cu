@@ -360,13 +360,18 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
                                             const uint32_t (&vim)[16])
 {
     if constexpr (NPOL == 1) {
-        // s1: this row's station; column 2j + p2 is station 2(s2_0 + j) + p2;
-        // one complex per baseline
+        // s1: this row's station; column k = 2j + p2 is station s2b + k with
+        // s2b = 2 s2_0; one complex per baseline. Twice the stores of the
+        // two-pol case, so their indices come from the group's first one,
+        // tri(s2b) + s1 with tri(s) = s(s+1)/2, as + k*s2b + k(k+1)/2: one
+        // independent multiply-add per store.
+        const int s2b = 2 * s2_0;
+        const long long base = unit_off + (long long)s2b * (s2b + 1) / 2 + s1;
+        const int lo = s1 - s2b, hi = P.S - s2b;   // valid columns: lo <= k < hi
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int s2 = 2 * s2_0 + k;
-            if (!(s1 <= s2 && s2 < P.S)) continue;
-            const long long e = unit_off + (long long)s2 * (s2 + 1) / 2 + s1;
+            if (k < lo || k >= hi) continue;
+            const long long e = base + (long long)(k * s2b + k * (k + 1) / 2);
             if (DT == 1) {
                 float2 *dst = static_cast<float2 *>(P.out) + e;
                 __stcs(dst, make_float2(__uint_as_float(vre[k]), __uint_as_float(vim[k])));

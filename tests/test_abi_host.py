@@ -99,7 +99,8 @@ def test_create_rejects_bad_descriptions_without_gpu(L):
     for d in bad:
         assert L.corr_create(ctypes.byref(d), ctypes.byref(h)) == 1
         assert not h.value
-    unsupported = [Desc(4, 1, 1, 1, 1, 0, 0, 0),   # one polarisation
+    unsupported = [Desc(4, 3, 1, 1, 1, 0, 0, 0),   # three polarisations
+                   Desc(4, 1, 1, 1, 1, 0, 1, 4 | 1),  # one pol with gain calibration
                    Desc(4, 2, 1, 1, 1, 1, 1, 0),   # FP16 on the FP32 path
                    Desc(4, 2, 1, 1, 1, 0, 2, 0),   # FP32 on the tensor path
                    Desc(4, 2, 1, 70000, 1, 2, 0, 0)]  # int8 with T beyond the INT32 range

@@ -123,3 +123,37 @@ def test_single_pol_batched_and_host_streaming():
     got = out.numpy().astype(np.int64)
     np.testing.assert_array_equal(got[..., 0].reshape(ref.shape), ref.real.astype(np.int64))
     np.testing.assert_array_equal(got[..., 1].reshape(ref.shape), ref.imag.astype(np.int64))
+
+
+@pytest.mark.parametrize("S,T,C,I", [(1, 5, 1, 1), (3, 33, 2, 1), (17, 100, 3, 2), (64, 768, 4, 1),
+                                     (129, 64, 1, 1), (200, 40, 1, 1)])
+def test_single_pol_fp32(S, T, C, I):
+    """FP32 CUDA-core path with one polarisation (pairs of stations staged as
+    the two pols of pseudo-stations by 8-byte asynchronous copies)."""
+    from paper_1702_00844_gb300 import Plan
+    from helpers import TOL_FP32
+    g = synth.rng(S * 3 + T)
+    x = (g.standard_normal((I, C, S, T, 1)) + 1j * g.standard_normal((I, C, S, T, 1))).astype(np.complex64)
+    plan = Plan(S, C, T, I, dtype="cf32", path="fp32", n_pols=1)
+    out = plan.empty_out()
+    out.fill_(float("nan"))
+    plan.correlate(torch.from_numpy(x).cuda(), out)
+    torch.cuda.synchronize()
+    plan.check_error()
+    got = out.cpu().numpy().reshape((I * C, S * (S + 1) // 2, 1, 1))
+    ref = oracle.correlate(x.reshape((I * C, S, T, 1)))
+    assert np.isfinite(got).all()
+    assert rel_frobenius_per_unit(got, ref).max() < TOL_FP32
+
+
+def test_single_pol_fp32_equals_xx_of_two_pols():
+    from paper_1702_00844_gb300 import Plan
+    S, C, T = 70, 3, 96
+    g = synth.rng(77)
+    x2 = (g.standard_normal((C, S, T, 2)) + 1j * g.standard_normal((C, S, T, 2))).astype(np.complex64)
+    x1 = np.ascontiguousarray(x2[..., :1])
+    o1 = Plan(S, C, T, dtype="cf32", path="fp32", n_pols=1).correlate(torch.from_numpy(x1).cuda())
+    o2 = Plan(S, C, T, dtype="cf32", path="fp32").correlate(torch.from_numpy(x2).cuda())
+    torch.cuda.synchronize()
+    a, b = o1[..., 0, 0].cpu().numpy(), o2[..., 0, 0].cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
