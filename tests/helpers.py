@@ -7,6 +7,16 @@ import numpy as np
 # values, so only the FP32 accumulation differs as well.
 TOL_FP32 = 1e-5
 TOL_FP16 = 1e-5
+
+
+def tol_fp16(T: int) -> float:
+    """FP16 inputs on the tensor path: every accumulator element receives T/8
+    MMA additions (four K=16 steps per block of 32 samples, for Re and for
+    Im), each rounding the FP32 running sum by at most one ulp (2^-23 of a
+    running sum that the autocorrelations bound by the final norm), so the
+    relative Frobenius error is at most (T/8) * 2^-23 = T * 2^-26; never
+    tighter than TOL_FP16."""
+    return max(TOL_FP16, T * 2.0 ** -26)
 # Element-wise bound on the correlation-coefficient error
 #   |dV_ab| <= TOL_COEF * sqrt(V_aa V_bb) * (number of terms)^0 ... (see below)
 TOL_COEF = 2e-5
