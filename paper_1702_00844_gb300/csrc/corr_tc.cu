@@ -470,6 +470,9 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
     const bool leader = rank == 0;
     const int item0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int item_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    // No work (e.g. an empty redo list): leave before any barrier, TMEM or
+    // cluster step. Both CTAs of a pair see the same item0 and leave together.
+    if (item0 >= n_items) return;
 
     // In a pair, the even CTA's full and acc_empty barriers also count one
     // arrival of the odd CTA's relay thread (see the relay below).
