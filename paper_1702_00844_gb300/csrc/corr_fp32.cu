@@ -5,6 +5,7 @@
 // accumulators kept in registers for the whole integration) and performs
 // the conjugate multiply-add with four FMAs,
 //     acc_r += a_r b_r + a_i b_i,   acc_i += a_i b_r - a_r b_i,
+// issued as two packed FP32x2 FMAs on the (acc_r, acc_i) pair,
 // reusing each loaded sample against 4 partner stations (Table 1, 4x4 tile:
 // 512 flops per 128 bytes loaded). Tiles in the same row of the triangle are
 // assigned to neighbouring threads so they consume the same samples at the
@@ -33,6 +34,25 @@
 namespace corr {
 
 namespace {
+
+__device__ __forceinline__ uint64_t pack2(float lo, float hi)
+{
+    uint64_t v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+    return v;
+}
+
+// (lo, hi) += (a.lo * b.lo, a.hi * b.hi): two fused multiply-adds, each
+// rounded to nearest, in one packed instruction.
+__device__ __forceinline__ void fma2(float &lo, float &hi, uint64_t a, uint64_t b)
+{
+    asm("{\n\t.reg .b64 q;\n\t"
+        "mov.b64 q, {%0, %1};\n\t"
+        "fma.rn.f32x2 q, %2, %3, q;\n\t"
+        "mov.b64 {%0, %1}, q;\n\t}"
+        : "+f"(lo), "+f"(hi)
+        : "l"(a), "l"(b));
+}
 
 __device__ __forceinline__ void decode_subtile(int nq, int k, int &i, int &j)
 {
@@ -172,21 +192,33 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
                 for (int a = 0; a < 4; ++a) r[a] = base[row_off[a] + t * 8];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) c[b] = base[col_off[b] + t * 8];
+                // The four FMAs of each complex multiply-add as two packed
+                // FMAs on the (re, im) accumulator pair of pol pair (p1, p2):
+                //   (re, im) += (r_re, r_im) * (c_re, c_re)
+                //   (re, im) += (r_im, -r_re) * (c_im, c_im)
+                // the same fused operations in the same order as
+                //   re += r_re c_re + r_im c_im,   im += r_im c_re - r_re c_im.
+                uint64_t R1[4][2], R2[4][2], C1[4][2], C2[4][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    R1[a][0] = pack2(r[a].x, r[a].y);
+                    R2[a][0] = pack2(r[a].y, -r[a].x);
+                    R1[a][1] = pack2(r[a].z, r[a].w);
+                    R2[a][1] = pack2(r[a].w, -r[a].z);
+                    C1[a][0] = pack2(c[a].x, c[a].x);
+                    C2[a][0] = pack2(c[a].y, c[a].y);
+                    C1[a][1] = pack2(c[a].z, c[a].z);
+                    C2[a][1] = pack2(c[a].w, c[a].w);
+                }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        float *q = acc[a][b];
-                        // (p1, p2) = (0,0), (0,1), (1,0), (1,1); entries (re, im)
-                        q[0] = fmaf(r[a].x, c[b].x, q[0]); q[0] = fmaf(r[a].y, c[b].y, q[0]);
-                        q[1] = fmaf(r[a].y, c[b].x, q[1]); q[1] = fmaf(-r[a].x, c[b].y, q[1]);
-                        q[2] = fmaf(r[a].x, c[b].z, q[2]); q[2] = fmaf(r[a].y, c[b].w, q[2]);
-                        q[3] = fmaf(r[a].y, c[b].z, q[3]); q[3] = fmaf(-r[a].x, c[b].w, q[3]);
-                        q[4] = fmaf(r[a].z, c[b].x, q[4]); q[4] = fmaf(r[a].w, c[b].y, q[4]);
-                        q[5] = fmaf(r[a].w, c[b].x, q[5]); q[5] = fmaf(-r[a].z, c[b].y, q[5]);
-                        q[6] = fmaf(r[a].z, c[b].z, q[6]); q[6] = fmaf(r[a].w, c[b].w, q[6]);
-                        q[7] = fmaf(r[a].w, c[b].z, q[7]); q[7] = fmaf(-r[a].z, c[b].w, q[7]);
-                    }
+                    for (int b = 0; b < 4; ++b)
+#pragma unroll
+                        for (int pp = 0; pp < 4; ++pp) { // (p1, p2) = (pp >> 1, pp & 1)
+                            fma2(acc[a][b][2 * pp], acc[a][b][2 * pp + 1], R1[a][pp >> 1], C1[b][pp & 1]);
+                            fma2(acc[a][b][2 * pp], acc[a][b][2 * pp + 1], R2[a][pp >> 1], C2[b][pp & 1]);
+                        }
             }
         }
         __syncthreads();
