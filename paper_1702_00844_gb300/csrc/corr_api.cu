@@ -31,8 +31,9 @@ struct corr_plan {
     int fp_threads = 0;
     size_t fp_smem = 0;
     // tensor path (single problem)
-    int4 *d_items = nullptr;
-    int n_items = 0;
+    int4 *d_items = nullptr;   // main list, then the tail list (pair variant)
+    int n_items = 0;           // main list
+    int n_tail = 0;            // tail list (narrow tiles of an odd last block column)
     int tc_variant = TC_NARROW;
     int pair_clusters = 0;     // clusters of the pair variant resident at once (0: unavailable)
     float tune_ms[TC_N_VARIANTS] = {0.f, 0.f, 0.f};
@@ -46,6 +47,7 @@ struct corr_plan {
     TcProblem *d_bprobs = nullptr;
     int4 *d_bitems = nullptr;
     int n_bitems = 0;
+    int n_btail = 0;
     int b_variant = TC_NARROW;
     // host-buffer streaming (CORR_FLAG_HOST_IO)
     int chunk_units = 0;
@@ -153,16 +155,21 @@ size_t out_unit_bytes(const corr_desc_t &d)
 // block rb and column blocks cb0..cb0+ncb-1 of 64 stations, rb <= cb0.
 // narrow: every (rb, cb) with rb <= cb; wide: column blocks taken in pairs
 // from the row block onward (the last one alone if the count is odd); pair:
-// row blocks {rb, rb+1} x column blocks {cb0, cb0+1} for even rb <= cb0 (a
-// block past the last holds no stations). Items are unit-major.
-std::vector<int4> tc_items_for(int prob, int S, int units, int variant)
+// row blocks {rb, rb+1} x column blocks {cb0, cb0+1} for even rb <= cb0 over
+// the first 2*floor(nb/2) blocks, and, when the block count nb is odd, the
+// last block column as narrow tiles (rb, nb-1) in *tail (a pair tile there
+// would hold a block without stations). Items are unit-major.
+std::vector<int4> tc_items_for(int prob, int S, int units, int variant, std::vector<int4> *tail)
 {
     std::vector<int4> v;
     const int nb = tc_blocks(S);
     for (int u = 0; u < units; ++u) {
         if (variant == TC_PAIR) {
-            for (int rb = 0; rb < nb; rb += 2)
-                for (int cb = rb; cb < nb; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
+            const int nbe = nb & ~1;
+            for (int rb = 0; rb < nbe; rb += 2)
+                for (int cb = rb; cb < nbe; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
+            if (nb & 1)
+                for (int rb = 0; rb < nb; ++rb) tail->push_back(make_int4(prob, u, rb, (nb - 1) | (1 << 16)));
         } else if (variant == TC_WIDE) {
             for (int rb = 0; rb < nb; ++rb)
                 for (int cb = rb; cb < nb; cb += 2) {
@@ -215,7 +222,7 @@ corr_status_t ensure_redo(corr_plan *h, int n)
     h->d_redo_items = nullptr;
     h->redo_cap = 0;
     corr_status_t st;
-    if (!h->d_redo_count && (st = cuda_status(cudaMalloc(&h->d_redo_count, sizeof(int)))) != CORR_OK) return st;
+    if (!h->d_redo_count && (st = cuda_status(cudaMalloc(&h->d_redo_count, 2 * sizeof(int)))) != CORR_OK) return st;
     if ((st = cuda_status(cudaMalloc(&h->d_redo_mark, (size_t)n * sizeof(int)))) != CORR_OK) return st;
     if ((st = cuda_status(cudaMalloc(&h->d_redo_items, (size_t)n * sizeof(int4)))) != CORR_OK) return st;
     h->redo_cap = n;
@@ -233,36 +240,57 @@ int tc_grid_for(const corr_plan *h, int variant, int n)
     return std::max(1, std::min(n, h->sm_count));
 }
 
-corr_status_t run_tensor(corr_plan *h, TcParams p, int dtype, int variant, int max_T, cudaStream_t s)
+// One item list in one tile variant. The int8 redo list of this launch uses
+// the plan's redo entries [redo_off, redo_off + p.n_items) and counter `ctr`.
+corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max_T, int redo_off,
+                       int ctr, cudaStream_t s)
 {
     if (variant == TC_PAIR && h->pair_clusters < 1) {
         set_last_error("the pair tile variant does not fit on this device");
         return CORR_ERR_UNSUPPORTED;
     }
     const int grid = tc_grid_for(h, variant, p.n_items);
-    const bool checked = dtype == CORR_CI8 && max_T > TC_INT8_CHUNK_KB * TC_KB_T && h->redo_cap >= p.n_items;
+    const bool checked = dtype == CORR_CI8 && max_T > TC_INT8_CHUNK_KB * TC_KB_T &&
+                         h->redo_cap >= redo_off + p.n_items;
     if (!checked) {
         p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
         return cuda_status(tc_launch(dtype, variant, h->d.n_pols, p, grid, s));
     }
-    corr_status_t st = cuda_status(cudaMemsetAsync(h->d_redo_mark, 0, (size_t)p.n_items * sizeof(int), s));
-    if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count, 0, sizeof(int), s));
+    corr_status_t st =
+        cuda_status(cudaMemsetAsync(h->d_redo_mark + redo_off, 0, (size_t)p.n_items * sizeof(int), s));
+    if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count + ctr, 0, sizeof(int), s));
     if (st != CORR_OK) return st;
     TcParams a = p;
     a.chunk_kb = 0;
     a.check_power = 1;
-    a.redo_mark = h->d_redo_mark;
-    a.redo_items = h->d_redo_items;
-    a.redo_count = h->d_redo_count;
+    a.redo_mark = h->d_redo_mark + redo_off;
+    a.redo_items = h->d_redo_items + redo_off;
+    a.redo_count = h->d_redo_count + ctr;
     st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
     if (st != CORR_OK) return st;
     TcParams b = p;
-    b.items = h->d_redo_items;
+    b.items = h->d_redo_items + redo_off;
     b.n_items = p.n_items;          // upper bound; the count is read on the device
-    b.n_items_dev = h->d_redo_count;
+    b.n_items_dev = h->d_redo_count + ctr;
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
     return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s));
+}
+
+// The main list of p in `variant`, then (pair variant) the n_tail narrow
+// tail items at `tail`.
+corr_status_t run_tensor(corr_plan *h, TcParams p, const int4 *tail, int n_tail, int dtype, int variant,
+                         int max_T, cudaStream_t s)
+{
+    corr_status_t st = CORR_OK;
+    if (p.n_items > 0) st = run_list(h, p, dtype, variant, max_T, 0, 0, s);
+    if (st == CORR_OK && n_tail > 0) {
+        TcParams q = p;
+        q.items = tail;
+        q.n_items = n_tail;
+        st = run_list(h, q, dtype, TC_NARROW, max_T, p.n_items, 1, s);
+    }
+    return st;
 }
 
 corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long long units,
@@ -288,11 +316,14 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     TcParams p{};
     p.prob0 = make_problem(d_in, d_out, d.n_stations, d.n_samples, (int)units, d.dtype, d.n_pols);
     p.probs = nullptr;
-    p.items = h->d_items; // unit-major, so the first units' items are a prefix
-    p.n_items = (int)((long long)h->n_items / ((long long)d.n_channels * d.n_integrations) * units);
+    // both lists are unit-major, so the first units' items are prefixes
+    const long long all_units = (long long)d.n_channels * d.n_integrations;
+    p.items = h->d_items;
+    p.n_items = (int)((long long)h->n_items / all_units * units);
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return run_tensor(h, p, d.dtype, h->tc_variant, d.n_samples, s);
+    return run_tensor(h, p, h->d_items + h->n_items, (int)((long long)h->n_tail / all_units * units),
+                      d.dtype, h->tc_variant, d.n_samples, s);
 }
 
 corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
@@ -302,16 +333,18 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
 
 
 // ------------------------------------------------------------------ autotuner
-// The tile variant of the tensor path is chosen per (device, dtype, S, T) by
-// timing the variants once on zero-filled samples of the plan's shape (about
-// four waves of work items over the SMs), unless CORR_TC_VARIANT=
+// The tile variant of the tensor path is chosen per (device, dtype, pols, S,
+// T, units) by
+// timing the variants once on zero-filled samples of the plan's shape (its
+// own size up to 2 GB), unless CORR_TC_VARIANT=
 // narrow|wide|pair forces one or CORR_FLAG_NO_AUTOTUNE asks for the
 // heuristic (pair from 128 stations). Choices are cached for the process.
 struct TuneKey {
     int dev, dtype, npol, S, T;
+    long long units; // the choice depends on the waves of work items too
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(dev, dtype, npol, S, T) < std::tie(o.dev, o.dtype, o.npol, o.S, o.T);
+        return std::tie(dev, dtype, npol, S, T, units) < std::tie(o.dev, o.dtype, o.npol, o.S, o.T, o.units);
     }
 };
 std::mutex g_tune_mu;
@@ -330,7 +363,10 @@ int forced_variant()
 corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, const void *d_in,
                            void *d_out, float *ms_out)
 {
-    std::vector<int4> items = tc_items_for(0, item_stations(S, h->d.n_pols), units, variant);
+    std::vector<int4> tail;
+    std::vector<int4> items = tc_items_for(0, item_stations(S, h->d.n_pols), units, variant, &tail);
+    const int n_main = (int)items.size(), n_tail = (int)tail.size();
+    items.insert(items.end(), tail.begin(), tail.end());
     int4 *d_items = nullptr;
     corr_status_t st = cuda_status(cudaMalloc(&d_items, items.size() * sizeof(int4)));
     if (st != CORR_OK) return st;
@@ -342,18 +378,18 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
         TcParams p{};
         p.prob0 = make_problem(d_in, d_out, S, T, units, h->d.dtype, h->d.n_pols);
         p.items = d_items;
-        p.n_items = (int)items.size();
+        p.n_items = n_main;
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
-        if (h->d.dtype == CORR_CI8 && (st = ensure_redo(h, p.n_items)) != CORR_OK) break;
+        if (h->d.dtype == CORR_CI8 && (st = ensure_redo(h, n_main + n_tail)) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
         for (int i = 0; i < 2 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, h->d.dtype, variant, T, 0);
+            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, variant, T, 0);
         if (st != CORR_OK) break;
         cudaEventRecord(e0, 0);
         for (int i = 0; i < 3 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, h->d.dtype, variant, T, 0);
+            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, variant, T, 0);
         cudaEventRecord(e1, 0);
         if (st != CORR_OK) break;
         if ((st = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
@@ -379,7 +415,8 @@ corr_status_t tune_tensor_variant(corr_plan *h)
         h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
         return CORR_OK;
     }
-    const TuneKey key{h->device, d.dtype, d.n_pols, d.n_stations, d.n_samples};
+    const TuneKey key{h->device, d.dtype, d.n_pols, d.n_stations, d.n_samples,
+                      (long long)d.n_channels * d.n_integrations};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -389,15 +426,27 @@ corr_status_t tune_tensor_variant(corr_plan *h)
         }
     }
     const long long units = (long long)d.n_channels * d.n_integrations;
-    const int nbu = tc_blocks(item_stations(d.n_stations, d.n_pols));
-    const long long per_unit = (long long)nbu * (nbu + 1) / 2;
-    const int su = (int)std::max(1LL, std::min(units, (4LL * h->sm_count + per_unit - 1) / per_unit));
-    const size_t in_bytes = (size_t)su * in_unit_bytes(d);
-    const size_t out_bytes = (size_t)su * out_unit_bytes(d);
+    // The plan's own unit count, up to 2 GB of zero-filled samples and
+    // visibilities: the variants' wave quantisation at the real size decides
+    // (the pair variant splits its work over two launches). If that memory is
+    // not free, a quarter of it, and otherwise the heuristic choice.
+    const long long fit = std::max(1LL, (2048LL << 20) / (long long)(in_unit_bytes(d) + out_unit_bytes(d)));
+    int su = (int)std::max(1LL, std::min(units, fit));
     void *d_in = nullptr, *d_out = nullptr;
-    corr_status_t st = cuda_status(cudaMalloc(&d_in, in_bytes));
-    if (st == CORR_OK) st = cuda_status(cudaMalloc(&d_out, out_bytes));
-    if (st == CORR_OK) st = cuda_status(cudaMemset(d_in, 0, in_bytes));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (cudaMalloc(&d_in, (size_t)su * in_unit_bytes(d)) == cudaSuccess &&
+            cudaMalloc(&d_out, (size_t)su * out_unit_bytes(d)) == cudaSuccess)
+            break;
+        cudaGetLastError();
+        cudaFree(d_in);
+        d_in = d_out = nullptr;
+        su = std::max(1, su / 4);
+    }
+    if (!d_in || !d_out) {
+        h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
+        return CORR_OK;
+    }
+    corr_status_t st = cuda_status(cudaMemset(d_in, 0, (size_t)su * in_unit_bytes(d)));
     for (int v = 0; v < TC_N_VARIANTS && st == CORR_OK; ++v) {
         h->tune_ms[v] = 0.f;
         if (v == TC_PAIR && h->pair_clusters < 1) continue;
@@ -538,15 +587,18 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             fp32_config(h);
         } else {
             if ((st = tune_tensor_variant(h)) != CORR_OK) break;
+            std::vector<int4> tail;
             std::vector<int4> items =
-                tc_items_for(0, item_stations(d.n_stations, d.n_pols), (int)units, h->tc_variant);
+                tc_items_for(0, item_stations(d.n_stations, d.n_pols), (int)units, h->tc_variant, &tail);
             h->n_items = (int)items.size();
+            h->n_tail = (int)tail.size();
+            items.insert(items.end(), tail.begin(), tail.end());
             if ((st = cuda_status(cudaMalloc(&h->d_items, items.size() * sizeof(int4)))) != CORR_OK)
                 break;
             if ((st = cuda_status(cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int4),
                                              cudaMemcpyHostToDevice))) != CORR_OK)
                 break;
-            if (d.dtype == CORR_CI8 && (st = ensure_redo(h, h->n_items)) != CORR_OK) break;
+            if (d.dtype == CORR_CI8 && (st = ensure_redo(h, h->n_items + h->n_tail)) != CORR_OK) break;
         }
         if (d.flags & CORR_FLAG_HOST_IO) {
             // chunks of about 32 MiB of input (CORR_HOST_CHUNK_MB overrides;
@@ -673,19 +725,21 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                                   : (big >= 0.5 * all ? big_v : TC_NARROW);
         }
         std::vector<TcProblem> probs;
-        std::vector<int4> items;
+        std::vector<int4> items, tail;
         for (int i = 0; i < n_sub; ++i) {
             const corr_subarray_t &s = subs[i];
             probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
                                          h->d.dtype, h->d.n_pols));
             if (s.n_samples == 0) continue;
-            std::vector<int4> v =
-                tc_items_for(i, item_stations(s.n_stations, h->d.n_pols), s.n_channels, h->b_variant);
+            std::vector<int4> v = tc_items_for(i, item_stations(s.n_stations, h->d.n_pols), s.n_channels,
+                                               h->b_variant, &tail);
             items.insert(items.end(), v.begin(), v.end());
         }
-        std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
-            return probs[a.x].T > probs[b.x].T;
-        });
+        auto heavier = [&](const int4 &a, const int4 &b) { return probs[a.x].T > probs[b.x].T; };
+        std::stable_sort(items.begin(), items.end(), heavier);
+        std::stable_sort(tail.begin(), tail.end(), heavier);
+        h->n_btail = (int)tail.size();
+        items.insert(items.end(), tail.begin(), tail.end());
         cudaFree(h->d_bprobs);
         cudaFree(h->d_bitems);
         h->d_bprobs = nullptr;
@@ -702,8 +756,8 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                                             cudaMemcpyHostToDevice))) != CORR_OK)
                 return e;
         }
-        h->n_bitems = (int)items.size();
-        if (h->d.dtype == CORR_CI8 && (e = ensure_redo(h, h->n_bitems)) != CORR_OK) return e;
+        h->n_bitems = (int)items.size() - h->n_btail;
+        if (h->d.dtype == CORR_CI8 && (e = ensure_redo(h, h->n_bitems + h->n_btail)) != CORR_OK) return e;
         h->batch_key.assign(subs, subs + n_sub);
     }
     for (int i = 0; i < n_sub; ++i)
@@ -713,7 +767,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
             corr_status_t e = cuda_status(cudaMemsetAsync(subs[i].d_out, 0, bytes, st));
             if (e != CORR_OK) return e;
         }
-    if (h->n_bitems == 0) return CORR_OK;
+    if (h->n_bitems + h->n_btail == 0) return CORR_OK;
     TcParams p{};
     p.probs = h->d_bprobs;
     p.items = h->d_bitems;
@@ -722,7 +776,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     p.wait_ns = h->wait_ns;
     int max_T = 0;
     for (int i = 0; i < n_sub; ++i) max_T = std::max(max_T, subs[i].n_samples);
-    return run_tensor(h, p, h->d.dtype, h->b_variant, max_T, st);
+    return run_tensor(h, p, h->d_bitems + h->n_bitems, h->n_btail, h->d.dtype, h->b_variant, max_T, st);
 }
 
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,

@@ -89,6 +89,19 @@ def test_int8_adversarial_extremes_chunk_fold(T, variant):
     exact_int(out, signs)
 
 
+@pytest.mark.parametrize("variant", ["pair"], indirect=True)
+def test_int8_extremes_odd_block_count_pair_and_tail(variant):
+    """Three 64-station blocks with the pair variant: pair tiles over the first
+    two blocks and narrow tiles for the last block column, in two launches
+    with their own redo lists. All-(+-127) samples over 1500 samples make
+    every tile of both lists fail the power check and take its chunked redo."""
+    S, C, T = 150, 2, 1500
+    g = synth.rng(63, T)
+    x = np.where(g.random((C, S, T, 2, 2)) < 0.5, -127, 127).astype(np.int8)
+    out = run_tc(x, S, C, T, "ci8", expect_variant="pair")
+    exact_int(out, x)
+
+
 def test_fp16_int_valued_exact_below_2pow24():
     """FP16 copies of int8 samples with T <= 512: exact integers in FP32."""
     S, T, C = 96, 512, 2
