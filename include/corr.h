@@ -106,10 +106,12 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out);
 
 /* Correlates all integrations and channels of the plan (Section 2, the
  * correlation formula; Fig. 2). d_in: input samples, layout and type as
- * above, n_integrations*n_channels*n_stations*n_samples*2 complex values;
- * d_out: visibilities, n_integrations*n_channels*S(S+1)/2*4 complex values,
- * fully overwritten. d_in may be NULL when n_samples is 0 (the output is
- * then all zeros). Asynchronous on stream; capturable in a CUDA graph. */
+ * above, n_integrations*n_channels*n_stations*n_samples*P complex values;
+ * d_out: visibilities, n_integrations*n_channels*S(S+1)/2*P*P complex
+ * values, fully overwritten. d_in may be NULL when n_samples is 0 (the
+ * output is then all zeros). Asynchronous on stream (one to four kernel
+ * launches and, for int8 with more than 512 samples, small memsets);
+ * capturable in a CUDA graph. */
 corr_status_t corr_correlate(corr_handle_t h, const void *d_in, void *d_out, void *stream);
 
 /* corr_correlate with HOST buffers (h_in, h_out: same layouts as above, in
@@ -127,7 +129,10 @@ corr_status_t corr_correlate_host(corr_handle_t h, const void *h_in, void *h_out
 /* Correlates a ragged batch of n_sub independent sub-arrays (each with its
  * own S, C and T, channels independent as in Section 2) in one persistent
  * kernel launch on the tensor path with the plan's dtype (CORR_CF16 or
- * CORR_CI8). The plan's own S, C and T are ignored. The first call with a
+ * CORR_CI8) and pol count (one launch per tile kind: with the pair variant,
+ * pair tiles and, for sub-arrays with an odd number of 64-station blocks,
+ * narrow tiles for the last block column). The plan's own S, C and T are
+ * ignored. The first call with a
  * new set of sub-arrays (shapes or pointers) builds and uploads the work
  * list and synchronizes; it must not be captured. Later calls with the same
  * set only launch and are capturable. */
