@@ -30,6 +30,7 @@ struct corr_plan {
     Fp32Params fp{};
     int fp_threads = 0;
     size_t fp_smem = 0;
+    float2 *d_fp_partial = nullptr; // partial sums of a split sample axis
     // tensor path (single problem)
     int4 *d_items = nullptr;   // main list, then the tail list (pair variant)
     int n_items = 0;           // main list
@@ -136,6 +137,19 @@ void fp32_config(corr_plan *h)
     while (tc > 1 && (size_t)FP32_STAGES * nbox * tc * 128 > 100 * 1024) tc >>= 1;
     p.tc = tc;
     h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;
+    // Few units (channels x integrations) leave SMs idle: then the sample
+    // axis is split into ranges of whole chunks over more CTAs (about two per
+    // SM), and a second kernel sums the partial results in order.
+    // CORR_FP32_KSPLIT forces a split count.
+    const int total = std::max(1, (p.T + tc - 1) / tc);
+    const long long ctas = (long long)p.n_units * p.groups;
+    int ks = 1;
+    if (p.T > 0 && ctas < 2LL * h->sm_count)
+        ks = (int)std::min<long long>(total, (2LL * h->sm_count + ctas - 1) / ctas);
+    if (const char *e = std::getenv("CORR_FP32_KSPLIT")) ks = std::max(1, std::min(total, std::atoi(e)));
+    p.kchunks = (total + ks - 1) / ks;
+    p.ksplit = (total + p.kchunks - 1) / p.kchunks;
+    p.partial = nullptr;
 }
 
 // Bytes of one station-time sample of all npol pols.
@@ -309,6 +323,7 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
         p.n_units = (int)units;
         p.out = static_cast<float2 *>(d_out);
         p.in1 = static_cast<const float2 *>(d_in);
+        p.partial = p.ksplit > 1 ? h->d_fp_partial : nullptr;
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
         return cuda_status(fp32_launch(&m, p, d.n_pols, h->fp_threads, h->fp_smem, s));
@@ -585,6 +600,10 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
         }
         if (path == CORR_PATH_FP32) {
             fp32_config(h);
+            if (h->fp.ksplit > 1 &&
+                (st = cuda_status(cudaMalloc(&h->d_fp_partial, (size_t)h->fp.ksplit * units *
+                                                                   out_unit_bytes(d)))) != CORR_OK)
+                break;
         } else {
             if ((st = tune_tensor_variant(h)) != CORR_OK) break;
             std::vector<int4> tail;
@@ -876,6 +895,7 @@ corr_status_t corr_destroy(corr_handle_t h)
     if (!h) return CORR_OK;
     cudaDeviceSynchronize();
     cudaFree(h->d_err);
+    cudaFree(h->d_fp_partial);
     cudaFree(h->d_items);
     cudaFree(h->d_redo_mark);
     cudaFree(h->d_redo_items);

@@ -28,6 +28,9 @@
 // threads of a quarter-warp read 8 distinct 16-byte bank groups; the rotation
 // is undone when the result is stored.
 #include <cuda.h>
+
+#include <algorithm>
+
 #include "corr_internal.h"
 #include "ptx.cuh"
 
@@ -110,8 +113,9 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
-    const int unit = blockIdx.x / p.groups;
     const int grp = blockIdx.x % p.groups;
+    const int unit = (blockIdx.x / p.groups) % p.n_units;
+    const int kpart = blockIdx.x / (p.groups * p.n_units);   // range of the sample axis
     const int k_first = grp * p.group_size;
     const int k = k_first + tid;
     const bool active = tid < p.group_size && k < p.nsub;
@@ -124,7 +128,9 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     const int box_f4 = p.tc * 8;                 // float4 per box
     const int stage_f4 = nbox * box_f4;
     const uint32_t stage_bytes = (uint32_t)stage_f4 * 16u;
-    const int nchunks = (p.T + p.tc - 1) / p.tc;
+    // this CTA's chunks: kc0 .. kc0 + nchunks - 1 of the whole sample axis
+    const int kc0 = kpart * p.kchunks;
+    const int nchunks = min(p.kchunks, (p.T + p.tc - 1) / p.tc - kc0);
 
     if (tid == 0) {
         if (NPOL == 2) prefetch_tmap(&tmap);
@@ -139,15 +145,15 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         mbar_arrive_expect_tx(&full[st], stage_bytes);
         for (int b = 0; b < nbox; ++b)
             tma_load_4d(smem + (size_t)st * stage_bytes + (size_t)b * box_f4 * 16, &tmap, &full[st],
-                        0, s_lo + 8 * b, kc * p.tc, unit);
+                        0, s_lo + 8 * b, (kc0 + kc) * p.tc, unit);
     };
     // NPOL = 1: every thread copies its share of the stage's (station, time)
     // values (time fastest, so a warp reads contiguous samples of a station);
     // one commit group per stage, zero fill outside the array.
     auto issue1 = [&](int kc) {
         stage_single_pol(smem_u32(smem) + (uint32_t)(kc % FP32_STAGES) * stage_bytes,
-                         p.in1 + (size_t)unit * p.S1 * p.T, p.in1, p.S1, p.T, p.tc, s_lo, nbox, kc,
-                         nchunks, tid, (int)blockDim.x);
+                         p.in1 + (size_t)unit * p.S1 * p.T, p.in1, p.S1, p.T, p.tc, s_lo, nbox, kc0 + kc,
+                         kc0 + nchunks, tid, (int)blockDim.x);
     };
     if (NPOL == 1) {
         for (int kc = 0; kc < FP32_STAGES; ++kc) issue1(kc);
@@ -184,7 +190,7 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         }
         if (ok) {
             const float4 *base = sm4 + (size_t)st * stage_f4;
-            const int tn = min(p.tc, p.T - kc * p.tc);
+            const int tn = min(p.tc, p.T - (kc0 + kc) * p.tc);
 #pragma unroll 1
             for (int t = 0; t < tn; ++t) {
                 float4 r[4], c[4];
@@ -241,7 +247,7 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         // pseudo rows 4i+a (stations 2(4i+a)+p1) x pseudo columns (stations
         // 2 col + p2); one complex per baseline
         const long long B1 = (long long)p.S1 * (p.S1 + 1) / 2;
-        float2 *out = p.out + (long long)unit * B1;
+        float2 *out = (p.partial ? p.partial + (long long)kpart * p.n_units * B1 : p.out) + (long long)unit * B1;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -258,7 +264,8 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         return;
     }
     const long long B = (long long)p.S * (p.S + 1) / 2;
-    float2 *out = p.out + (long long)unit * B * 4;
+    float2 *out = (p.partial ? p.partial + (long long)kpart * p.n_units * B * 4 : p.out) +
+                  (long long)unit * B * 4;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int s1 = 4 * i + a;
@@ -276,23 +283,53 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
 
 } // namespace
 
+// out[i] = sum over k of partial[k][i], k in order (deterministic).
+__global__ void __launch_bounds__(256) fp32_reduce_kernel(const float2 *__restrict__ partial,
+                                                          float2 *__restrict__ out, long long n, int ksplit)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 a = __ldg(partial + i);
+        for (int k = 1; k < ksplit; ++k) {
+            const float2 b = __ldg(partial + (long long)k * n + i);
+            a.x += b.x;
+            a.y += b.y;
+        }
+        out[i] = a;
+    }
+}
+
+// Sums the ksplit partial results of a launch: units x baselines x pol
+// pairs complex values each.
+cudaError_t fp32_reduce(const Fp32Params &p, int npol, cudaStream_t s)
+{
+    const long long B = (long long)p.S1 * (p.S1 + 1) / 2;
+    const long long n = (long long)p.n_units * B * npol * npol;
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 8);
+    fp32_reduce_kernel<<<(unsigned)std::max(1LL, blocks), 256, 0, s>>>(p.partial, p.out, n, p.ksplit);
+    return cudaGetLastError();
+}
+
 cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int threads, size_t smem,
                         cudaStream_t s)
 {
+    const unsigned grid = (unsigned)(p.n_units * p.groups * p.ksplit);
     if (npol == 1) {
         cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         CUtensorMap unused{};
-        fp32_correlate_kernel<1><<<p.n_units * p.groups, threads, smem, s>>>(unused, p);
-        return cudaGetLastError();
+        fp32_correlate_kernel<1><<<grid, threads, smem, s>>>(unused, p);
+        e = cudaGetLastError();
+        return (e == cudaSuccess && p.partial) ? fp32_reduce(p, npol, s) : e;
     }
     cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    fp32_correlate_kernel<2><<<p.n_units * p.groups, threads, smem, s>>>(*m, p);
-    return cudaGetLastError();
+    fp32_correlate_kernel<2><<<grid, threads, smem, s>>>(*m, p);
+    e = cudaGetLastError();
+    return (e == cudaSuccess && p.partial) ? fp32_reduce(p, npol, s) : e;
 }
 
 } // namespace corr

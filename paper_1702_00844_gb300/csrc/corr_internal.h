@@ -65,6 +65,11 @@ struct Fp32Params {
     // real station count (S = ceil(S1 / 2) pseudo-stations)
     const float2 *in1;
     int S1;
+    // split of the sample axis over CTAs (few units): ksplit ranges of
+    // kchunks chunks each, partial sums in partial[ksplit][n_units][...],
+    // summed in a fixed order by a second kernel (nullptr when ksplit = 1)
+    int ksplit, kchunks;
+    float2 *partial;
 };
 constexpr int FP32_STAGES = 3;
 // npol 2: samples through the TMA map tmap; npol 1: through p.in1.
