@@ -12,6 +12,7 @@
 // The input gradient is a complex GEMM per channel: W' = 2 conj(g) W g is
 // formed once, then grad_x[c][t] = sum_b W'[c][b] x[b][t].
 #include "corr_internal.h"
+#include "ptx.cuh"
 
 namespace corr {
 
@@ -149,7 +150,9 @@ __global__ void build_w_kernel(const float2 *R, const float2 *g, const float2 *M
 }
 
 // grad_x[unit][s][t][p] = sum_b W'[unit][(s,p)][b] x[unit][b][t], b = (s', p').
-// CTA tile: 64 rows (c) x 64 times; thread tile 4 rows x 4 times.
+// CTA tile: 64 rows (c) x 64 times; thread tile 4 rows x 4 times. The b axis
+// goes through shared memory 16 at a time in two stages: the asynchronous
+// copies of step k + 1 are in flight while step k is computed.
 __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, const float2 *x,
                                                               float2 *gx, int S, int T)
 {
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, c
     const float2 *Wu = W + (long long)unit * N * N;
     const float2 *xu = x + (long long)unit * S * T * 2;
     float2 *gu = gx + (long long)unit * S * T * 2;
-    __shared__ float2 Ws[64][17];
-    __shared__ float2 Xs[16][64];
+    __shared__ float2 Ws[2][64][17];
+    __shared__ float2 Xs[2][16][64];
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     float2 acc[4][4];
@@ -170,27 +173,43 @@ __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, c
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
 
-    for (int b0 = 0; b0 < N; b0 += 16) {
+    // Stage the W' and x tiles of columns b0 .. b0+15 (zero outside the
+    // matrix: a copy with no source bytes fills zeros and reads nothing).
+    auto stage = [&](int st, int b0) {
+#pragma unroll
         for (int e = tid; e < 64 * 16; e += 256) {
             const int r = e >> 4, k = e & 15;
             const int c = c0 + r, b = b0 + k;
-            Ws[r][k] = (c < N && b < N) ? Wu[(long long)c * N + b] : make_float2(0.f, 0.f);
+            const bool in = c < N && b < N;
+            cp_async_small<8>(smem_u32(&Ws[st][r][k]), in ? Wu + (long long)c * N + b : Wu, in ? 8u : 0u);
         }
+#pragma unroll
         for (int e = tid; e < 16 * 64; e += 256) {
             // e -> (station-local, t, pol) in memory order of x
             const int sl = e >> 7, rem = e & 127, tt = rem >> 1, pp = rem & 1;
             const int s = (b0 >> 1) + sl, t = t0 + tt;
-            Xs[2 * sl + pp][tt] = (s < S && t < T) ? xu[((long long)s * T + t) * 2 + pp]
-                                                   : make_float2(0.f, 0.f);
+            const bool in = s < S && t < T;
+            cp_async_small<8>(smem_u32(&Xs[st][2 * sl + pp][tt]),
+                              in ? xu + ((long long)s * T + t) * 2 + pp : xu, in ? 8u : 0u);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    stage(0, 0);
+    for (int b0 = 0, st = 0; b0 < N; b0 += 16, st ^= 1) {
+        if (b0 + 16 < N) {
+            stage(st ^ 1, b0 + 16);   // that buffer was released by the barrier closing the last step
+            cp_async_wait<1>();       // this thread's copies of step b0 have landed
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();              // ... and everyone else's
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             float2 wv[4], xv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) wv[a] = Ws[ty * 4 + a][k];
+            for (int a = 0; a < 4; ++a) wv[a] = Ws[st][ty * 4 + a][k];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) xv[q] = Xs[k][tx * 4 + q];
+            for (int q = 0; q < 4; ++q) xv[q] = Xs[st][k][tx * 4 + q];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
