@@ -30,12 +30,11 @@
 // Warp roles (416 threads):
 //   warps 0-7  : stage raw samples with 16-byte asynchronous copies into a
 //                per-thread ring in shared memory (each thread later converts
-//                exactly the bytes it copied, so the ring needs no barrier),
+//                exactly the bytes it copied, so the ring needs no barrier;
+//                int8 pair tiles load into a ring of registers instead),
 //                widen int8 to f16 exactly, split polarisations and
 //                real/imaginary parts, and store the operand tiles in the
 //                128-byte swizzled K-major layout of a ring of operand stages.
-//                (Loads into registers would be drained by every release
-//                arrive on the stage barrier; asynchronous copies are not.)
 //   warps 8-11 : epilogue: TMEM -> registers, mask s1 <= s2, store
 //                [channel][baseline][p1][p2] once (int8: fold each 512-sample
 //                chunk into INT32 exactly);
@@ -89,22 +88,42 @@ template <int DT> struct RawBytes { static constexpr int value = DT == 1 ? 64 : 
 #ifndef CORR_TC_RAW_PAIR_I8
 #define CORR_TC_RAW_PAIR_I8 5
 #endif
-constexpr int MAX_OPS = 4; // size of the stage barrier arrays
+// int8 pair producers load samples straight into a ring of registers (PF
+// K-blocks ahead) instead of staging them in shared memory (RAW = 0 selects
+// it). The freed shared memory deepens the operand ring. On the 256-station
+// workload this measured 1-2% faster for pair tiles and slower for narrow and
+// wide tiles, which keep the asynchronous-copy ring.
+#ifndef CORR_TC_REGPF
+#define CORR_TC_REGPF 1
+#endif
+#ifndef CORR_TC_PF
+#define CORR_TC_PF 4
+#endif
+#ifndef CORR_TC_OPS_REG_PAIR_I8
+#define CORR_TC_OPS_REG_PAIR_I8 6
+#endif
+constexpr int MAX_OPS = 6; // size of the stage barrier arrays
 template <int DT, int V> struct Cfg;
 template <> struct Cfg<1, TC_NARROW> {
     static constexpr int OPS = CORR_TC_OPS_F16, RAW = CORR_TC_RAW_F16, MAXB = 1, NBUF = 2;
 };
-template <> struct Cfg<2, TC_NARROW> {
-    static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, MAXB = 1, NBUF = 2;
-};
 template <> struct Cfg<1, TC_WIDE> { static constexpr int OPS = 2, RAW = 2, MAXB = 2, NBUF = 1; };
-template <> struct Cfg<2, TC_WIDE> { static constexpr int OPS = 3, RAW = 3, MAXB = 2, NBUF = 1; };
 template <> struct Cfg<1, TC_PAIR> {
     static constexpr int OPS = CORR_TC_OPS_PAIR_F16, RAW = CORR_TC_RAW_PAIR_F16, MAXB = 1, NBUF = 1;
 };
+template <> struct Cfg<2, TC_NARROW> {
+    static constexpr int OPS = CORR_TC_OPS_I8, RAW = CORR_TC_RAW_I8, MAXB = 1, NBUF = 2;
+};
+template <> struct Cfg<2, TC_WIDE> { static constexpr int OPS = 3, RAW = 3, MAXB = 2, NBUF = 1; };
+#if CORR_TC_REGPF
+template <> struct Cfg<2, TC_PAIR> {
+    static constexpr int OPS = CORR_TC_OPS_REG_PAIR_I8, RAW = 0, MAXB = 1, NBUF = 1;
+};
+#else
 template <> struct Cfg<2, TC_PAIR> {
     static constexpr int OPS = CORR_TC_OPS_PAIR_I8, RAW = CORR_TC_RAW_PAIR_I8, MAXB = 1, NBUF = 1;
 };
+#endif
 
 template <int DT, int V> __host__ __device__ constexpr int stage_bytes()
 {
@@ -131,7 +150,8 @@ struct Bars {
 
 template <int DT, int V> constexpr bool cfg_ok()
 {
-    return Cfg<DT, V>::OPS >= 2 && Cfg<DT, V>::OPS <= MAX_OPS && Cfg<DT, V>::RAW >= 2 &&
+    return Cfg<DT, V>::OPS >= 2 && Cfg<DT, V>::OPS <= MAX_OPS &&
+           (Cfg<DT, V>::RAW >= 2 || (Cfg<DT, V>::RAW == 0 && DT == 2)) &&
            smem_bytes<DT, V>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
 }
 static_assert(cfg_ok<1, TC_NARROW>() && cfg_ok<2, TC_NARROW>() && cfg_ok<1, TC_WIDE>() &&
@@ -235,6 +255,60 @@ __device__ __forceinline__ void read_raw(uint32_t src, uint32_t chunk_stride, Ra
 {
 #pragma unroll
     for (int q = 0; q < RawBytes<DT>::value / 16; ++q) r.v[q] = lds128(src + q * chunk_stride);
+}
+
+// Loads into registers the bytes that issue_raw<2, NPOL> copies for one unit
+// (int8 samples; the same chunk order and the same zero fill outside
+// [0,S) x [0,T)). Rows of whole 16-byte chunks take 16-byte loads where the
+// chunk is in range, other samples plain loads of their own size.
+template <int NPOL>
+__device__ __forceinline__ void load_raw_i8(const uint8_t *unit_in, int S, int T, bool vec, int s, int t0,
+                                            int g, Raw<2> &r)
+{
+    if constexpr (NPOL == 1) {
+        // chunk p: samples t0 + 8g .. +7 of station 2s + p, 2 bytes each
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int st = 2 * s + p;
+            const bool srow = st < S;
+            const uint8_t *row = unit_in + (srow ? (size_t)st * T * 2 : 0);
+            const int tq = t0 + 8 * g;
+            if (vec && srow && tq + 8 <= T) {
+                r.v[p] = __ldg(reinterpret_cast<const uint4 *>(row + (size_t)tq * 2));
+            } else {
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ta = tq + 2 * i;
+                    const uint32_t lo = (srow && ta < T)
+                        ? __ldg(reinterpret_cast<const unsigned short *>(row + (size_t)ta * 2)) : 0u;
+                    const uint32_t hi = (srow && ta + 1 < T)
+                        ? __ldg(reinterpret_cast<const unsigned short *>(row + (size_t)(ta + 1) * 2)) : 0u;
+                    w[i] = lo | (hi << 16);
+                }
+                r.v[p] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        return;
+    }
+    const bool srow = s < S;
+    const uint8_t *row = unit_in + (srow ? (size_t)s * T * 4 : 0);
+    if (vec && srow && t0 + TC_KB_T <= T) {  // whole K-block in range
+        const uint4 *src = reinterpret_cast<const uint4 *>(row + (size_t)t0 * 4 + g * 16);
+        r.v[0] = __ldg(src);
+        r.v[1] = __ldg(src + 4);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int tq = t0 + (g + 4 * q) * 4;   // 4 samples of 4 bytes per chunk
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                w[i] = (srow && tq + i < T) ? __ldg(reinterpret_cast<const unsigned int *>(row + (size_t)(tq + i) * 4))
+                                            : 0u;
+            r.v[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
 }
 
 // Two int8 (as the low bytes of the two halves of u) -> two exact f16:
@@ -540,7 +614,7 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
 #pragma unroll
             for (int j = 1; j < NSLOT; ++j) st_of[j] = (b_first + j - 1) * TC_RS + sl;
             auto slot_addr = [&](int k, int j) {
-                return raw_base + (uint32_t)((k % RAW) * NSLOT + j) * SLOT + (uint32_t)pt * 16u;
+                return raw_base + (uint32_t)((k % (RAW > 0 ? RAW : 1)) * NSLOT + j) * SLOT + (uint32_t)pt * 16u;
             };
             auto issue_kb = [&](int k) {
                 if (k < nkb) {
@@ -552,22 +626,10 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
                 }
                 cp_async_commit(); // one group per K-block (empty past the end)
             };
-#pragma unroll 1
-            for (int q = 0; q < RAW - 1; ++q) issue_kb(q);
             bool ok = true;
-#pragma unroll 1
-            for (int k = 0; k < nkb; ++k) {
-                issue_kb(k + RAW - 1);
-                cp_async_wait<RAW - 1>(); // this thread's copies of K-block k have landed
-                Raw<DT> r[NSLOT];
-#pragma unroll
-                for (int j = 0; j < NSLOT; ++j)
-                    if (j <= nB) read_raw<DT>(slot_addr(k, j), CHUNK, r[j]);
-                if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
-                                       p.wait_ns)) {
-                    ok = false;
-                    break;
-                }
+            // Converts K-block data r into operand stage `stage`, adds its
+            // power and publishes the stage to the MMA thread.
+            auto produce = [&](const Raw<DT> (&r)[NSLOT]) {
                 const uint32_t st = tiles_u32 + stage * STAGE;
 #pragma unroll
                 for (int j = 0; j < NSLOT; ++j)
@@ -585,15 +647,70 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
                                 power[j] = __dp4a((int)r[j].v[q].w, (int)r[j].v[q].w, power[j]);
                             }
                 }
+            };
+            auto publish = [&]() {
                 fence_proxy_async_smem();
                 mbar_arrive(&bars->full[stage]);
                 if (++stage == OPS) {
                     stage = 0;
                     phase ^= 1;
                 }
+            };
+            if constexpr (RAW == 0) {
+                // int8: a ring of PF K-blocks in registers. The loads of
+                // K-block k + PF are issued once K-block k is converted, so
+                // each has PF K-block periods to arrive; a stage barrier
+                // arrival does not wait for them.
+                constexpr int PF = CORR_TC_PF;
+                Raw<DT> ring[PF][NSLOT];
+                auto load_kb = [&](int k, Raw<DT> (&dst)[NSLOT]) {
+                    if (k < nkb) {
+#pragma unroll
+                        for (int j = 0; j < NSLOT; ++j)
+                            if (j <= nB) load_raw_i8<NPOL>(unit_in, P.S, P.T, vec, st_of[j], k * TC_KB_T, g, dst[j]);
+                    }
+                };
+#pragma unroll
+                for (int d = 0; d < PF; ++d) load_kb(d, ring[d]);
+#pragma unroll 1
+                for (int k0 = 0; k0 < nkb && ok; k0 += PF) {
+#pragma unroll
+                    for (int d = 0; d < PF; ++d) {
+                        if (k0 + d < nkb && ok) {
+                            if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
+                                                   p.wait_ns)) {
+                                ok = false;
+                            } else {
+                                produce(ring[d]);
+                                load_kb(k0 + d + PF, ring[d]);
+                                publish();
+                            }
+                        }
+                    }
+                }
+                if (!ok) break;
+            } else {
+#pragma unroll 1
+                for (int q = 0; q < RAW - 1; ++q) issue_kb(q);
+#pragma unroll 1
+                for (int k = 0; k < nkb; ++k) {
+                    issue_kb(k + RAW - 1);
+                    cp_async_wait<RAW - 1>(); // this thread's copies of K-block k have landed
+                    Raw<DT> r[NSLOT];
+#pragma unroll
+                    for (int j = 0; j < NSLOT; ++j)
+                        if (j <= nB) read_raw<DT>(slot_addr(k, j), CHUNK, r[j]);
+                    if (!mbar_wait_bounded(&bars->empty[stage], phase ^ 1, abort_flag, p.err,
+                                           p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    produce(r);
+                    publish();
+                }
+                cp_async_wait<0>();
+                if (!ok) break;
             }
-            cp_async_wait<0>();
-            if (!ok) break;
             if (check) {
                 // station power = sum over the 4 threads of the station (both
                 // pols together, which bounds each pol); any station above
