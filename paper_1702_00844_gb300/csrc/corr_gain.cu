@@ -150,26 +150,34 @@ __global__ void build_w_kernel(const float2 *R, const float2 *g, const float2 *M
 }
 
 // grad_x[unit][s][t][p] = sum_b W'[unit][(s,p)][b] x[unit][b][t], b = (s', p').
-// CTA tile: 64 rows (c) x 64 times; thread tile 4 rows x 4 times. The b axis
-// goes through shared memory 16 at a time in two stages: the asynchronous
-// copies of step k + 1 are in flight while step k is computed.
+// CTA tile: 16 TM rows (c) x 64 times; thread tile TM rows x 4 times. The b
+// axis goes through shared memory 16 at a time in two stages: the
+// asynchronous copies of step k + 1 are in flight while step k is computed.
+// W' is staged k-major, so that a thread's TM rows at one k are contiguous.
+#ifndef CORR_IG_TM
+#define CORR_IG_TM 8
+#endif
+template <int TM>
 __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, const float2 *x,
                                                               float2 *gx, int S, int T)
 {
+    constexpr int BM = 16 * TM;
+    constexpr int WLD = BM + 2;   // padded row: the staging writes of one k spread over banks
     const int N = 2 * S;
     const int unit = blockIdx.z;
-    const int c0 = blockIdx.y * 64;
+    const int c0 = blockIdx.y * BM;
     const int t0 = blockIdx.x * 64;
     const float2 *Wu = W + (long long)unit * N * N;
     const float2 *xu = x + (long long)unit * S * T * 2;
     float2 *gu = gx + (long long)unit * S * T * 2;
-    __shared__ float2 Ws[2][64][17];
-    __shared__ float2 Xs[2][16][64];
+    extern __shared__ __align__(16) float2 ig_smem[];
+    float2 (*Ws)[16][WLD] = reinterpret_cast<float2 (*)[16][WLD]>(ig_smem);          // [2][16][WLD]
+    float2 (*Xs)[16][64] = reinterpret_cast<float2 (*)[16][64]>(ig_smem + 2 * 16 * WLD); // [2][16][64]
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
-    float2 acc[4][4];
+    float2 acc[TM][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
 
@@ -177,11 +185,11 @@ __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, c
     // matrix: a copy with no source bytes fills zeros and reads nothing).
     auto stage = [&](int st, int b0) {
 #pragma unroll
-        for (int e = tid; e < 64 * 16; e += 256) {
+        for (int e = tid; e < BM * 16; e += 256) {
             const int r = e >> 4, k = e & 15;
             const int c = c0 + r, b = b0 + k;
             const bool in = c < N && b < N;
-            cp_async_small<8>(smem_u32(&Ws[st][r][k]), in ? Wu + (long long)c * N + b : Wu, in ? 8u : 0u);
+            cp_async_small<8>(smem_u32(&Ws[st][k][r]), in ? Wu + (long long)c * N + b : Wu, in ? 8u : 0u);
         }
 #pragma unroll
         for (int e = tid; e < 16 * 64; e += 256) {
@@ -205,13 +213,21 @@ __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, c
         __syncthreads();              // ... and everyone else's
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            float2 wv[4], xv[4];
+            float2 wv[TM], xv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) wv[a] = Ws[st][ty * 4 + a][k];
+            for (int a = 0; a < TM; a += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(&Ws[st][k][ty * TM + a]);
+                wv[a] = make_float2(v.x, v.y);
+                wv[a + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) xv[q] = Xs[st][k][tx * 4 + q];
+            for (int q = 0; q < 4; q += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(&Xs[st][k][tx * 4 + q]);
+                xv[q] = make_float2(v.x, v.y);
+                xv[q + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < TM; ++a)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     acc[a][q].x = fmaf(wv[a].x, xv[q].x, fmaf(-wv[a].y, xv[q].y, acc[a][q].x));
@@ -221,8 +237,8 @@ __global__ void __launch_bounds__(256) input_grad_gemm_kernel(const float2 *W, c
         __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int c = c0 + ty * 4 + a;
+    for (int a = 0; a < TM; ++a) {
+        const int c = c0 + ty * TM + a;
         if (c >= N) continue;
         const int s = c >> 1, pp = c & 1;
 #pragma unroll
@@ -260,8 +276,13 @@ cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
     const long long n = (long long)units * N * N;
     build_w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, g, M, scale, W, S, units);
     if (T > 0) {
-        dim3 grid((T + 63) / 64, (unsigned)((N + 63) / 64), units);
-        input_grad_gemm_kernel<<<grid, 256, 0, s>>>(W, x, grad_x, S, T);
+        constexpr int BM = 16 * CORR_IG_TM;
+        constexpr size_t smem = (size_t)(2 * 16 * (BM + 2) + 2 * 16 * 64) * sizeof(float2);
+        cudaError_t e = cudaFuncSetAttribute(input_grad_gemm_kernel<CORR_IG_TM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((T + 63) / 64, (unsigned)((N + BM - 1) / BM), units);
+        input_grad_gemm_kernel<CORR_IG_TM><<<grid, 256, smem, s>>>(W, x, grad_x, S, T);
     }
     return cudaGetLastError();
 }
