@@ -12,7 +12,10 @@
 // same time (Section 2's inter-tile reuse through co-scheduling).
 //
 // Registers are capped at 168 per thread and CTAs at 192 threads so that two
-// CTAs share an SM (at most 3 warps per SM sub-partition).
+// CTAs share an SM (at most 3 warps per SM sub-partition). Up to 64 stations
+// the sub-tiles are 4 x 2 stations instead (64 accumulators, 112 registers,
+// CTAs of up to 288 threads): the same FMAs per accumulator in the same
+// order, on more threads.
 //
 // One polarisation (NPOL = 1): stations 2m and 2m+1 act as the two pols of
 // pseudo-station m. A box of 16 stations x tc samples of 8-byte complex
@@ -57,16 +60,25 @@ __device__ __forceinline__ void fma2(float &lo, float &hi, uint64_t a, uint64_t 
         : "l"(a), "l"(b));
 }
 
-__device__ __forceinline__ void decode_subtile(int nq, int k, int &i, int &j)
+// Sub-tile k of the row-major upper triangle of 4 x TW-station sub-tiles:
+// row i (stations 4i .. 4i+3) holds column groups j = 4i/TW .. ncq-1 (stations
+// TW j .. TW j + TW - 1).
+template <int TW> __device__ __forceinline__ void decode_subtile(int ncq, int k, int &i, int &j)
 {
-    // row-major upper triangle: row i holds columns i..nq-1
     int row = 0, off = 0;
-    while (k >= off + (nq - row)) {
-        off += nq - row;
+    while (k >= off + (ncq - 4 * row / TW)) {
+        off += ncq - 4 * row / TW;
         ++row;
     }
     i = row;
-    j = row + (k - off);
+    j = 4 * row / TW + (k - off);
+}
+
+// Column station of sub-tile column j, lane b, rotated so that the 8 threads
+// of a quarter-warp (consecutive j) read 8 distinct 16-byte bank groups.
+template <int TW> __device__ __forceinline__ int col_station(int j, int b)
+{
+    return TW * j + (TW == 4 ? ((b + (j >> 1)) & 3) : ((b + (j >> 2)) & 1));
 }
 
 // Waits for the TMA loads of chunks kc .. kc + STAGES - 1 (those issued by
@@ -102,9 +114,12 @@ __device__ __noinline__ void stage_single_pol(uint32_t base, const float2 *in1u,
     cp_async_commit();
 }
 
-template <int NPOL>
-__global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                             const Fp32Params p)
+// TW = 4: 4 x 4-station sub-tiles (128 accumulators, 168 registers, CTAs of
+// at most 192 threads); TW = 2: 4 x 2 (64 accumulators, 112 registers, CTAs of
+// at most 288 threads), more warps per SM for the same shared memory.
+template <int NPOL, int TW>
+__global__ void __maxnreg__(TW == 4 ? 168 : 112) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                       const Fp32Params p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -121,8 +136,8 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     const bool active = tid < p.group_size && k < p.nsub;
 
     int i, j, i_first, j_first;
-    decode_subtile(p.nq, active ? k : k_first, i, j);
-    decode_subtile(p.nq, k_first, i_first, j_first);
+    decode_subtile<TW>(p.ncq, active ? k : k_first, i, j);
+    decode_subtile<TW>(p.ncq, k_first, i_first, j_first);
     const int s_lo = (4 * i_first) & ~7;
     const int nbox = (p.S - s_lo + 7) / 8;
     const int box_f4 = p.tc * 8;                 // float4 per box
@@ -161,20 +176,23 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
         for (int kc = 0; kc < FP32_STAGES && kc < nchunks; ++kc) issue(kc);
     }
 
-    int row_off[4], col_off[4];
+    int row_off[4], col_off[TW];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int r = 4 * i + a - s_lo;
         row_off[a] = (r >> 3) * box_f4 + (r & 7);
-        const int c = 4 * j + ((a + (j >> 1)) & 3) - s_lo;
-        col_off[a] = (c >> 3) * box_f4 + (c & 7);
+    }
+#pragma unroll
+    for (int b = 0; b < TW; ++b) {
+        const int c = col_station<TW>(j, b) - s_lo;
+        col_off[b] = (c >> 3) * box_f4 + (c & 7);
     }
 
-    float acc[4][4][8];
+    float acc[4][TW][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+        for (int b = 0; b < TW; ++b)
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[a][b][q] = 0.f;
 
@@ -193,33 +211,36 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
             const int tn = min(p.tc, p.T - (kc0 + kc) * p.tc);
 #pragma unroll 1
             for (int t = 0; t < tn; ++t) {
-                float4 r[4], c[4];
+                float4 r[4], c[TW];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) r[a] = base[row_off[a] + t * 8];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) c[b] = base[col_off[b] + t * 8];
+                for (int b = 0; b < TW; ++b) c[b] = base[col_off[b] + t * 8];
                 // The four FMAs of each complex multiply-add as two packed
                 // FMAs on the (re, im) accumulator pair of pol pair (p1, p2):
                 //   (re, im) += (r_re, r_im) * (c_re, c_re)
                 //   (re, im) += (r_im, -r_re) * (c_im, c_im)
                 // the same fused operations in the same order as
                 //   re += r_re c_re + r_im c_im,   im += r_im c_re - r_re c_im.
-                uint64_t R1[4][2], R2[4][2], C1[4][2], C2[4][2];
+                uint64_t R1[4][2], R2[4][2], C1[TW][2], C2[TW][2];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     R1[a][0] = pack2(r[a].x, r[a].y);
                     R2[a][0] = pack2(r[a].y, -r[a].x);
                     R1[a][1] = pack2(r[a].z, r[a].w);
                     R2[a][1] = pack2(r[a].w, -r[a].z);
-                    C1[a][0] = pack2(c[a].x, c[a].x);
-                    C2[a][0] = pack2(c[a].y, c[a].y);
-                    C1[a][1] = pack2(c[a].z, c[a].z);
-                    C2[a][1] = pack2(c[a].w, c[a].w);
+                }
+#pragma unroll
+                for (int b = 0; b < TW; ++b) {
+                    C1[b][0] = pack2(c[b].x, c[b].x);
+                    C2[b][0] = pack2(c[b].y, c[b].y);
+                    C1[b][1] = pack2(c[b].z, c[b].z);
+                    C2[b][1] = pack2(c[b].w, c[b].w);
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
+                    for (int b = 0; b < TW; ++b)
 #pragma unroll
                         for (int pp = 0; pp < 4; ++pp) { // (p1, p2) = (pp >> 1, pp & 1)
                             fma2(acc[a][b][2 * pp], acc[a][b][2 * pp + 1], R1[a][pp >> 1], C1[b][pp & 1]);
@@ -251,8 +272,8 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int m1 = 4 * i + a, m2 = 4 * j + ((b + (j >> 1)) & 3);
+            for (int b = 0; b < TW; ++b) {
+                const int m1 = 4 * i + a, m2 = col_station<TW>(j, b);
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) {
                     const int s1 = 2 * m1 + (pp >> 1), s2 = 2 * m2 + (pp & 1);
@@ -270,8 +291,8 @@ __global__ void __maxnreg__(168) fp32_correlate_kernel(const __grid_constant__ C
     for (int a = 0; a < 4; ++a) {
         const int s1 = 4 * i + a;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int s2 = 4 * j + ((b + (j >> 1)) & 3);
+        for (int b = 0; b < TW; ++b) {
+            const int s2 = col_station<TW>(j, b);
             if (s1 <= s2 && s2 < p.S) {
                 float4 *dst = reinterpret_cast<float4 *>(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4);
                 dst[0] = make_float4(acc[a][b][0], acc[a][b][1], acc[a][b][2], acc[a][b][3]);
@@ -310,26 +331,33 @@ cudaError_t fp32_reduce(const Fp32Params &p, int npol, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+
+template <int NPOL, int TW>
+cudaError_t launch_tw(const void *tmap, const Fp32Params &p, int threads, size_t smem, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)(p.n_units * p.groups * p.ksplit);
+    cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<NPOL, TW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (NPOL == 1) {
+        CUtensorMap unused{};
+        fp32_correlate_kernel<NPOL, TW><<<grid, threads, smem, s>>>(unused, p);
+    } else {
+        fp32_correlate_kernel<NPOL, TW><<<grid, threads, smem, s>>>(*static_cast<const CUtensorMap *>(tmap), p);
+    }
+    e = cudaGetLastError();
+    return (e == cudaSuccess && p.partial) ? fp32_reduce(p, NPOL, s) : e;
+}
+
+} // namespace
+
 cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int threads, size_t smem,
                         cudaStream_t s)
 {
-    const unsigned grid = (unsigned)(p.n_units * p.groups * p.ksplit);
-    if (npol == 1) {
-        cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<1>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        CUtensorMap unused{};
-        fp32_correlate_kernel<1><<<grid, threads, smem, s>>>(unused, p);
-        e = cudaGetLastError();
-        return (e == cudaSuccess && p.partial) ? fp32_reduce(p, npol, s) : e;
-    }
-    cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    fp32_correlate_kernel<2><<<grid, threads, smem, s>>>(*m, p);
-    e = cudaGetLastError();
-    return (e == cudaSuccess && p.partial) ? fp32_reduce(p, npol, s) : e;
+    if (npol == 1)
+        return p.tw == 2 ? launch_tw<1, 2>(tmap, p, threads, smem, s) : launch_tw<1, 4>(tmap, p, threads, smem, s);
+    return p.tw == 2 ? launch_tw<2, 2>(tmap, p, threads, smem, s) : launch_tw<2, 4>(tmap, p, threads, smem, s);
 }
 
 } // namespace corr

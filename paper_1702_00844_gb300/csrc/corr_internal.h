@@ -57,7 +57,9 @@ cudaError_t tc_pair_max_clusters(int dtype, int *n);
 struct Fp32Params {
     float2 *out;
     int S, T, n_units;                // S: (pseudo-)stations of the sub-tile grid
-    int nq, nsub, groups, group_size; // 4x4 sub-tiles per unit and grouping
+    int tw;                           // sub-tiles of 4 x tw stations (tw = 4 or 2)
+    int nq, ncq;                      // row groups (4 stations) and column groups (tw)
+    int nsub, groups, group_size;     // sub-tiles per unit and their grouping over CTAs
     int tc;                           // samples per pipeline stage
     int *err;
     unsigned long long wait_ns;

@@ -99,3 +99,30 @@ def test_split_sample_axis_matches_oracle(monkeypatch, ks, npol):
     got = out.cpu().numpy().reshape(ref.shape)
     assert np.isfinite(got).all()
     assert rel_frobenius_per_unit(got, ref).max() < TOL_FP32
+
+
+@pytest.mark.parametrize("S,npol", [(8, 2), (37, 2), (64, 2), (65, 2), (130, 2), (61, 1), (200, 1)])
+def test_subtile_widths_bit_identical(monkeypatch, S, npol):
+    """4 x 4- and 4 x 2-station sub-tiles run each accumulator's FMAs in the
+    same order, so both give the same bits (station counts on and off the
+    sub-tile grid, both pol counts), and both match the oracle."""
+    from paper_1702_00844_gb300 import Plan
+    monkeypatch.setenv("CORR_FP32_KSPLIT", "1")
+    C, T = 3, 200
+    g = synth.rng(120 + S, npol)
+    x = (g.standard_normal((C, S, T, npol)) + 1j * g.standard_normal((C, S, T, npol))).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    outs = {}
+    for tw in ("4", "2"):
+        monkeypatch.setenv("CORR_FP32_TW", tw)
+        plan = Plan(S, C, T, dtype="cf32", path="fp32", n_pols=npol)
+        out = plan.empty_out()
+        out.fill_(float("nan"))
+        plan.correlate(xd, out)
+        torch.cuda.synchronize()
+        plan.check_error()
+        outs[tw] = out
+    assert torch.equal(outs["4"], outs["2"])
+    ref = oracle.correlate(x)
+    got = outs["2"].cpu().numpy().reshape(ref.shape)
+    assert rel_frobenius_per_unit(got, ref).max() < TOL_FP32
