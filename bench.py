@@ -37,7 +37,7 @@ WORKLOAD = ("precision: 256 stations, 2 pols, 480 channels, 1024 samples per int
             "complex int8 N(0,32^2) clipped to +-127, INT32 visibilities (bit-exact)")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tc_pair_kernel_int8_precision.txt")
 TC_SOURCES = [os.path.join(ROOT, "paper_1702_00844_gb300", "csrc", f)
-              for f in ("corr_tc.cu", "ptx.cuh", "corr_internal.h")]
+              for f in ("corr_tc.cu", "ptx.cuh", "corr_tc_internal.h")]
 
 
 def parse():

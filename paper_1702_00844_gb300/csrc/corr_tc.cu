@@ -42,7 +42,7 @@
 //                Im 128) columns; wide and pair: 1 buffer x (Re 256 + Im 256))
 //                and issues the MMAs (one thread; in a pair, of the even CTA).
 // Every wait is bounded (see mbar_wait_bounded).
-#include "corr_internal.h"
+#include "corr_tc_internal.h"
 #include "ptx.cuh"
 
 namespace corr {
