@@ -223,7 +223,7 @@ const char *corr_last_error_message(void);
  * convention and layouts) for n_units channels of n_stations stations and
  * n_samples samples, with d_raw_vis (R from corr_correlate) required.
  *
- * Scratch (the input-gradient matrix W', 16*S*S*n_units bytes when
+ * Scratch (the input-gradient matrix W', 32*S*S*n_units bytes when
  * d_grad_in is given, and one float per channel when d_loss is given) lives
  * in a fixed array of corr_noalloc_scratch_bytes() bytes (16 MiB) that the
  * library holds on every GPU that loads it, until the process exits. Larger

@@ -60,8 +60,8 @@ def test_noalloc_rejects_problems_beyond_the_fixed_array():
     from paper_1702_00844_gb300 import lib
     L = lib()
     cap = L.corr_noalloc_scratch_bytes()
-    S = 512                       # W' is 16*S*S bytes per channel = 4 MiB
-    C = cap // (16 * S * S) + 1   # one channel more than fits
+    S = 512                       # W' is (2S)^2 complex64 = 32*S*S bytes per channel = 8 MiB
+    C = cap // (32 * S * S) + 1   # one channel more than fits
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
     p = _vp(dummy)
     st = L.corr_gain_backward_noalloc(S, C, 8, p, p, p, p, p, p, None, None, None)
