@@ -278,7 +278,8 @@ def secondary(x8, torch):
     ms = time_launches(g.replay, 5, 2, torch.cuda.current_stream())
     opsb = sum(ops_of(S, T, C) for S, C, T in shapes)
     res["tensor_fp16_ragged_batch"] = {"ms": ms, "TOPS": opsb / ms / 1e9, "ops": opsb,
-                                       "input_GB": sum(x.numel() * 2 for x in xs) / 1e9}
+                                       "input_GB": sum(x.numel() * 2 for x in xs) / 1e9,
+                                       "variant": pb.batch_tile_variant()}
     pb.check_error()
     del xs, outs, pairs, g, pb
     torch.cuda.empty_cache()

@@ -134,8 +134,12 @@ corr_status_t corr_correlate_host(corr_handle_t h, const void *h_in, void *h_out
  * narrow tiles for the last block column). The plan's own S, C and T are
  * ignored. The first call with a
  * new set of sub-arrays (shapes or pointers) builds and uploads the work
- * list and synchronizes; it must not be captured. Later calls with the same
- * set only launch and are capturable. */
+ * list and synchronizes; it must not be captured. It also picks the tile
+ * variant for this set by timing each variant on the batch itself (one
+ * warm-up and one timed run each, whose results the final run overwrites),
+ * unless the plan has CORR_FLAG_NO_AUTOTUNE or CORR_TC_VARIANT forces one;
+ * corr_batch_tile_variant reports the choice. Later calls with the same set
+ * only launch and are capturable. */
 corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_subarray_t *subs,
                                      void *stream);
 
@@ -201,6 +205,11 @@ corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_
  * CORR_TC_VARIANT=narrow|wide|pair forces one (pair falls back to wide where
  * a cluster of two such CTAs cannot be resident). */
 int corr_tile_variant(corr_handle_t h);
+
+/* Tile variant of the plan's current ragged batch (same codes as
+ * corr_tile_variant), chosen on the first corr_correlate_batched call with
+ * that set of sub-arrays; -1 before any batch or for NULL. */
+int corr_batch_tile_variant(corr_handle_t h);
 
 /* Reads and clears the plan's device error word (synchronous copy):
  * CORR_OK or CORR_ERR_TIMEOUT. */

@@ -72,6 +72,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
     L.corr_tile_variant.argtypes = [vp]
     L.corr_tile_variant.restype = ip
+    L.corr_batch_tile_variant.argtypes = [vp]
+    L.corr_batch_tile_variant.restype = ip
     L.corr_tc_tiles.argtypes = [ip]
     L.corr_tc_tile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_fp32_subtiles.argtypes = [ip]
@@ -234,6 +236,11 @@ class Plan:
     def tile_variant(self) -> str:
         v = self.L.corr_tile_variant(self.h)
         return {0: "narrow", 1: "wide", 2: "pair"}.get(v, "fp32")
+
+    def batch_tile_variant(self) -> Optional[str]:
+        """Tile variant of the current ragged batch (None before any)."""
+        v = self.L.corr_batch_tile_variant(self.h)
+        return {0: "narrow", 1: "wide", 2: "pair"}.get(v)
 
     def check_error(self):
         _check(self.L.corr_get_error(self.h), "corr_get_error")

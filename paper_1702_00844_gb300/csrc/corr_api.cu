@@ -50,6 +50,7 @@ struct corr_plan {
     int n_bitems = 0;
     int n_btail = 0;
     int b_variant = TC_NARROW;
+    float b_tune_ms[TC_N_VARIANTS] = {};  // batch variant timings (0: not timed)
     // host-buffer streaming (CORR_FLAG_HOST_IO)
     int chunk_units = 0;
     void *d_stage_in[2] = {nullptr, nullptr};
@@ -716,6 +717,81 @@ corr_status_t corr_correlate_host(corr_handle_t h, const void *h_in, void *h_out
     return st;
 }
 
+} // extern "C"
+
+namespace {
+
+// Work list of a ragged batch in tile variant v: tiles of all sub-arrays,
+// heaviest (longest integration) first so that the static round-robin split
+// over the persistent CTAs ends evenly; the narrow tail items last.
+corr_status_t batch_items(corr_plan *h, int n_sub, const corr_subarray_t *subs, int v)
+{
+    std::vector<int4> items, tail;
+    std::vector<int> T(n_sub);
+    for (int i = 0; i < n_sub; ++i) {
+        T[i] = subs[i].n_samples;
+        if (subs[i].n_samples == 0) continue;
+        std::vector<int4> u = tc_items_for(i, item_stations(subs[i].n_stations, h->d.n_pols),
+                                           subs[i].n_channels, v, &tail);
+        items.insert(items.end(), u.begin(), u.end());
+    }
+    auto heavier = [&](const int4 &a, const int4 &b) { return T[a.x] > T[b.x]; };
+    std::stable_sort(items.begin(), items.end(), heavier);
+    std::stable_sort(tail.begin(), tail.end(), heavier);
+    h->n_btail = (int)tail.size();
+    h->n_bitems = (int)items.size();
+    items.insert(items.end(), tail.begin(), tail.end());
+    cudaFree(h->d_bitems);
+    h->d_bitems = nullptr;
+    corr_status_t e;
+    if (!items.empty()) {
+        if ((e = cuda_status(cudaMalloc(&h->d_bitems, items.size() * sizeof(int4)))) != CORR_OK) return e;
+        if ((e = cuda_status(cudaMemcpy(h->d_bitems, items.data(), items.size() * sizeof(int4),
+                                        cudaMemcpyHostToDevice))) != CORR_OK)
+            return e;
+    }
+    if (h->d.dtype == CORR_CI8 && (e = ensure_redo(h, h->n_bitems + h->n_btail)) != CORR_OK) return e;
+    return CORR_OK;
+}
+
+corr_status_t run_batch(corr_plan *h, int max_T, cudaStream_t st)
+{
+    if (h->n_bitems + h->n_btail == 0) return CORR_OK;
+    TcParams p{};
+    p.probs = h->d_bprobs;
+    p.items = h->d_bitems;
+    p.n_items = h->n_bitems;
+    p.err = h->d_err;
+    p.wait_ns = h->wait_ns;
+    return run_tensor(h, p, h->d_bitems + h->n_bitems, h->n_btail, h->d.dtype, h->b_variant, max_T, st);
+}
+
+// One warm-up run and one timed run of the current batch work list.
+corr_status_t time_batch(corr_plan *h, int max_T, cudaStream_t st, float *ms_out)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    corr_status_t e = CORR_OK;
+    do {
+        if ((e = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
+        if ((e = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
+        if ((e = run_batch(h, max_T, st)) != CORR_OK) break;
+        if ((e = cuda_status(cudaEventRecord(e0, st))) != CORR_OK) break;
+        if ((e = run_batch(h, max_T, st)) != CORR_OK) break;
+        if ((e = cuda_status(cudaEventRecord(e1, st))) != CORR_OK) break;
+        if ((e = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *ms_out = ms;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
+
+} // namespace
+
+extern "C" {
+
 corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_subarray_t *subs,
                                      void *stream)
 {
@@ -735,14 +811,37 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
     bool same = (int)h->batch_key.size() == n_sub;
     for (int i = 0; same && i < n_sub; ++i)
         same = std::memcmp(&h->batch_key[i], &subs[i], sizeof(corr_subarray_t)) == 0;
+    int max_T = 0;
+    for (int i = 0; i < n_sub; ++i) max_T = std::max(max_T, subs[i].n_samples);
     if (!same) {
-        // Build the ragged work list: tiles of all sub-arrays, heaviest (longest
-        // integration) first so that the static round-robin split over the
-        // persistent CTAs ends evenly. One tile variant serves the whole batch:
-        // pair (wide if pairs do not fit) when most of the work is in
+        h->batch_key.clear();
+        std::vector<TcProblem> probs;
+        for (int i = 0; i < n_sub; ++i) {
+            const corr_subarray_t &s = subs[i];
+            probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
+                                         h->d.dtype, h->d.n_pols));
+        }
+        cudaFree(h->d_bprobs);
+        h->d_bprobs = nullptr;
+        corr_status_t e;
+        if ((e = cuda_status(cudaMalloc(&h->d_bprobs, probs.size() * sizeof(TcProblem)))) != CORR_OK) return e;
+        if ((e = cuda_status(cudaMemcpy(h->d_bprobs, probs.data(), probs.size() * sizeof(TcProblem),
+                                        cudaMemcpyHostToDevice))) != CORR_OK)
+            return e;
+        // One tile variant serves the whole batch. Forced by CORR_TC_VARIANT;
+        // otherwise timed on this batch (each variant once to warm up, once
+        // timed; the sub-arrays' outputs are simply overwritten), unless the
+        // plan skips tuning or the stream is being captured, where pair (wide
+        // if pairs do not fit) is taken when most of the work is in
         // sub-arrays of >= 128 stations.
-        {
-            const int f = forced_variant();
+        const int f = forced_variant();
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if ((e = cuda_status(cudaStreamIsCapturing(st, &cap))) != CORR_OK) return e;
+        const int big_v = h->pair_clusters > 0 ? TC_PAIR : TC_WIDE;
+        for (int v = 0; v < TC_N_VARIANTS; ++v) h->b_tune_ms[v] = 0.f;
+        if (f >= 0) {
+            h->b_variant = (f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f;
+        } else {
             double big = 0, all = 0;
             for (int i = 0; i < n_sub; ++i) {
                 const double w = (double)n_baselines(subs[i].n_stations) * subs[i].n_samples *
@@ -750,44 +849,20 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                 all += w;
                 if (subs[i].n_stations >= 128) big += w;
             }
-            const int big_v = h->pair_clusters > 0 ? TC_PAIR : TC_WIDE;
-            h->b_variant = f >= 0 ? ((f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f)
-                                  : (big >= 0.5 * all ? big_v : TC_NARROW);
+            h->b_variant = big >= 0.5 * all ? big_v : TC_NARROW;
+            if (!(h->d.flags & CORR_FLAG_NO_AUTOTUNE) && cap == cudaStreamCaptureStatusNone && max_T > 0) {
+                int best = -1;
+                for (int v = 0; v < TC_N_VARIANTS; ++v) {
+                    if (v == TC_PAIR && h->pair_clusters < 1) continue;
+                    h->b_variant = v;
+                    if ((e = batch_items(h, n_sub, subs, v)) != CORR_OK) return e;
+                    if ((e = time_batch(h, max_T, st, &h->b_tune_ms[v])) != CORR_OK) return e;
+                    if (best < 0 || h->b_tune_ms[v] < h->b_tune_ms[best]) best = v;
+                }
+                h->b_variant = best >= 0 ? best : h->b_variant;
+            }
         }
-        std::vector<TcProblem> probs;
-        std::vector<int4> items, tail;
-        for (int i = 0; i < n_sub; ++i) {
-            const corr_subarray_t &s = subs[i];
-            probs.push_back(make_problem(s.d_in, s.d_out, s.n_stations, s.n_samples, s.n_channels,
-                                         h->d.dtype, h->d.n_pols));
-            if (s.n_samples == 0) continue;
-            std::vector<int4> v = tc_items_for(i, item_stations(s.n_stations, h->d.n_pols), s.n_channels,
-                                               h->b_variant, &tail);
-            items.insert(items.end(), v.begin(), v.end());
-        }
-        auto heavier = [&](const int4 &a, const int4 &b) { return probs[a.x].T > probs[b.x].T; };
-        std::stable_sort(items.begin(), items.end(), heavier);
-        std::stable_sort(tail.begin(), tail.end(), heavier);
-        h->n_btail = (int)tail.size();
-        items.insert(items.end(), tail.begin(), tail.end());
-        cudaFree(h->d_bprobs);
-        cudaFree(h->d_bitems);
-        h->d_bprobs = nullptr;
-        h->d_bitems = nullptr;
-        h->batch_key.clear();
-        corr_status_t e;
-        if ((e = cuda_status(cudaMalloc(&h->d_bprobs, probs.size() * sizeof(TcProblem)))) != CORR_OK) return e;
-        if ((e = cuda_status(cudaMemcpy(h->d_bprobs, probs.data(), probs.size() * sizeof(TcProblem),
-                                        cudaMemcpyHostToDevice))) != CORR_OK)
-            return e;
-        if (!items.empty()) {
-            if ((e = cuda_status(cudaMalloc(&h->d_bitems, items.size() * sizeof(int4)))) != CORR_OK) return e;
-            if ((e = cuda_status(cudaMemcpy(h->d_bitems, items.data(), items.size() * sizeof(int4),
-                                            cudaMemcpyHostToDevice))) != CORR_OK)
-                return e;
-        }
-        h->n_bitems = (int)items.size() - h->n_btail;
-        if (h->d.dtype == CORR_CI8 && (e = ensure_redo(h, h->n_bitems + h->n_btail)) != CORR_OK) return e;
+        if ((e = batch_items(h, n_sub, subs, h->b_variant)) != CORR_OK) return e;
         h->batch_key.assign(subs, subs + n_sub);
     }
     for (int i = 0; i < n_sub; ++i)
@@ -797,16 +872,7 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
             corr_status_t e = cuda_status(cudaMemsetAsync(subs[i].d_out, 0, bytes, st));
             if (e != CORR_OK) return e;
         }
-    if (h->n_bitems + h->n_btail == 0) return CORR_OK;
-    TcParams p{};
-    p.probs = h->d_bprobs;
-    p.items = h->d_bitems;
-    p.n_items = h->n_bitems;
-    p.err = h->d_err;
-    p.wait_ns = h->wait_ns;
-    int max_T = 0;
-    for (int i = 0; i < n_sub; ++i) max_T = std::max(max_T, subs[i].n_samples);
-    return run_tensor(h, p, h->d_bitems + h->n_bitems, h->n_btail, h->d.dtype, h->b_variant, max_T, st);
+    return run_batch(h, max_T, st);
 }
 
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
@@ -885,6 +951,12 @@ int corr_tile_variant(corr_handle_t h)
 {
     if (!h) return -1;
     return h->path == CORR_PATH_TENSOR ? h->tc_variant : -1;
+}
+
+int corr_batch_tile_variant(corr_handle_t h)
+{
+    if (!h || h->batch_key.empty()) return -1;
+    return h->b_variant;
 }
 
 corr_status_t corr_get_error(corr_handle_t h)

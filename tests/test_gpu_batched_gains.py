@@ -61,6 +61,36 @@ def test_ragged_batch_one_launch(dtype, variant, monkeypatch):
     check_batch(dtype, outs, hosts)
 
 
+@pytest.mark.parametrize("dtype", ["cf16", "ci8"])
+def test_ragged_batch_autotuned_variant(dtype, monkeypatch):
+    """Without a forced variant the first call times each tile variant on the
+    batch itself, keeps the fastest, and the final run's results are exact;
+    with the autotuner off the size rule picks one; a forced one is kept."""
+    from paper_1702_00844_gb300 import FLAG_NO_AUTOTUNE, Plan
+    monkeypatch.delenv("CORR_TC_VARIANT", raising=False)
+    for flags, want in ((0, None), (FLAG_NO_AUTOTUNE, None), (0, "wide")):
+        if want:
+            monkeypatch.setenv("CORR_TC_VARIANT", want)
+        plan = Plan(1, 1, 1, dtype=dtype, path="tensor", flags=flags)
+        assert plan.batch_tile_variant() is None
+        xs, outs, hosts = make_batch(dtype)
+        plan.correlate_batched(list(zip(xs, outs)), RAGGED)
+        torch.cuda.synchronize()
+        plan.check_error()
+        picked = plan.batch_tile_variant()
+        assert picked in ("narrow", "wide", "pair")
+        if want:
+            assert picked == want
+        check_batch(dtype, outs, hosts)
+        # a second call reuses the choice and the work list
+        for o in outs:
+            o.fill_(0)
+        plan.correlate_batched(list(zip(xs, outs)), RAGGED)
+        torch.cuda.synchronize()
+        assert plan.batch_tile_variant() == picked
+        check_batch(dtype, outs, hosts)
+
+
 def test_ragged_batch_graph_replay():
     """The work list is built on the first call; later calls are captured in a
     CUDA graph and replayed with identical results."""
