@@ -829,8 +829,8 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                                         cudaMemcpyHostToDevice))) != CORR_OK)
             return e;
         // One tile variant serves the whole batch. Forced by CORR_TC_VARIANT;
-        // otherwise timed on this batch (each variant once to warm up, once
-        // timed; the sub-arrays' outputs are simply overwritten), unless the
+        // otherwise timed on this batch (two rounds; each run warms up once
+        // and times once; the sub-arrays' outputs are simply overwritten), unless the
         // plan skips tuning or the stream is being captured, where pair (wide
         // if pairs do not fit) is taken when most of the work is in
         // sub-arrays of >= 128 stations.
@@ -849,17 +849,24 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
                 all += w;
                 if (subs[i].n_stations >= 128) big += w;
             }
-            h->b_variant = big >= 0.5 * all ? big_v : TC_NARROW;
+            const int rule = big >= 0.5 * all ? big_v : TC_NARROW;
+            h->b_variant = rule;
             if (!(h->d.flags & CORR_FLAG_NO_AUTOTUNE) && cap == cudaStreamCaptureStatusNone && max_T > 0) {
-                int best = -1;
-                for (int v = 0; v < TC_N_VARIANTS; ++v) {
-                    if (v == TC_PAIR && h->pair_clusters < 1) continue;
-                    h->b_variant = v;
-                    if ((e = batch_items(h, n_sub, subs, v)) != CORR_OK) return e;
-                    if ((e = time_batch(h, max_T, st, &h->b_tune_ms[v])) != CORR_OK) return e;
-                    if (best < 0 || h->b_tune_ms[v] < h->b_tune_ms[best]) best = v;
-                }
-                h->b_variant = best >= 0 ? best : h->b_variant;
+                // two rounds over the variants, each variant's best time
+                // counts; within 2% of the best, the size rule's choice stays
+                for (int round = 0; round < 2; ++round)
+                    for (int v = 0; v < TC_N_VARIANTS; ++v) {
+                        if (v == TC_PAIR && h->pair_clusters < 1) continue;
+                        h->b_variant = v;
+                        if ((e = batch_items(h, n_sub, subs, v)) != CORR_OK) return e;
+                        float ms = 0.f;
+                        if ((e = time_batch(h, max_T, st, &ms)) != CORR_OK) return e;
+                        if (round == 0 || ms < h->b_tune_ms[v]) h->b_tune_ms[v] = ms;
+                    }
+                int best = rule;
+                for (int v = 0; v < TC_N_VARIANTS; ++v)
+                    if (h->b_tune_ms[v] > 0.f && h->b_tune_ms[v] < 0.98f * h->b_tune_ms[best]) best = v;
+                h->b_variant = best;
             }
         }
         if ((e = batch_items(h, n_sub, subs, h->b_variant)) != CORR_OK) return e;
