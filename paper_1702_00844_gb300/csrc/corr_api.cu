@@ -914,13 +914,12 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     }
     const float2 *g = static_cast<const float2 *>(d_gain);
     const float2 *M = static_cast<const float2 *>(d_vis_model);
-    corr_status_t e = cuda_status(gain_grad_launch(R, g, M, d_grad_scale,
-                                                   static_cast<float2 *>(d_grad_gain), S, units, st));
+    corr_status_t e = cuda_status(gain_grad_launch(R, g, M, d_grad_scale, static_cast<float2 *>(d_grad_gain),
+                                                   d_grad_in ? h->d_W : nullptr, S, units, st));
     if (e != CORR_OK) return e;
     if (d_grad_in) {
-        e = cuda_status(input_grad_launch(static_cast<const float2 *>(d_in), R, g, M, d_grad_scale,
-                                          h->d_W, static_cast<float2 *>(d_grad_in), S,
-                                          h->d.n_samples, units, st));
+        e = cuda_status(input_grad_launch(static_cast<const float2 *>(d_in), h->d_W,
+                                          static_cast<float2 *>(d_grad_in), S, h->d.n_samples, units, st));
         if (e != CORR_OK) return e;
     }
     if (d_loss)

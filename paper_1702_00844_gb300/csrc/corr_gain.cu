@@ -82,71 +82,61 @@ __global__ void sum_partials_kernel(const float *partial, int n, float *loss)
     if (threadIdx.x == 0) *loss = red[0];
 }
 
-// One thread per (unit, c = (s, p)): both sums of dL/d conj(g_c).
-__global__ void gain_grad_kernel(const float2 *R, const float2 *g, const float2 *M,
-                                 const float *scale, float2 *grad, int S, int units)
+// One CTA per (unit, row c = (s, p)), its threads over b: the residuals of
+// row c give both sums of dL/d conj(g_c) (reduced over b in a fixed order)
+// and, when W is given, the row W'[unit][c][:] = 2 scale conj(g_c) W_cb g_b of
+// the input gradient.
+__global__ void __launch_bounds__(256) gain_grad_w_kernel(const float2 *R, const float2 *g, const float2 *M,
+                                                          const float *scale, float2 *grad, float2 *W, int S)
 {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int N = 2 * S;
-    if (idx >= (long long)units * N) return;
-    const int unit = (int)(idx / N);
-    const int c = (int)(idx % N);
+    const int c = (int)(blockIdx.x % (unsigned)N), unit = (int)(blockIdx.x / (unsigned)N);
     const int sc = c >> 1, pc = c & 1;
     const long long B4 = (long long)S * (S + 1) / 2 * 4;
     const float2 *Ru = R + unit * B4;
     const float2 *Mu = M + unit * B4;
     const float2 *gu = g + (long long)unit * N;
+    const float s = 2.f * (scale ? *scale : 1.f);
+    const float2 gc = cconj(gu[c]);
     float2 acc = make_float2(0.f, 0.f);
-    for (int b = 0; b < N; ++b) {
+    for (int b = threadIdx.x; b < N; b += blockDim.x) {
         const int sb = b >> 1, pb = b & 1;
+        const float2 gb = gu[b];
+        float2 w = make_float2(0.f, 0.f);
         if (sc <= sb) { // (c, b) in the triangle: E_cb g_b conj(R_cb)
+            const long long k = bl(sc, sb) * 4 + pc * 2 + pb;
             const float2 e = residual(Ru, gu, Mu, sc, pc, sb, pb);
-            const float2 r = Ru[bl(sc, sb) * 4 + pc * 2 + pb];
-            const float2 t = cmul(cmul(e, gu[b]), cconj(r));
+            const float2 t = cmul(cmul(e, gb), cconj(Ru[k]));
             acc.x += t.x;
             acc.y += t.y;
+            w.x += e.x;
+            w.y += e.y;
         }
         if (sb <= sc) { // (b, c) in the triangle: conj(E_bc) g_b R_bc
+            const long long k = bl(sb, sc) * 4 + pb * 2 + pc;
             const float2 e = residual(Ru, gu, Mu, sb, pb, sc, pc);
-            const float2 r = Ru[bl(sb, sc) * 4 + pb * 2 + pc];
-            const float2 t = cmul(cmul(cconj(e), gu[b]), r);
+            const float2 t = cmul(cmul(cconj(e), gb), Ru[k]);
             acc.x += t.x;
             acc.y += t.y;
+            w.x += e.x;
+            w.y -= e.y;
+        }
+        if (W) {
+            const float2 v = cmul(cmul(gc, w), gb);
+            W[((long long)unit * N + c) * N + b] = make_float2(s * v.x, s * v.y);
         }
     }
-    const float s = 2.f * (scale ? *scale : 1.f);
-    grad[idx] = make_float2(s * acc.x, s * acc.y);
-}
-
-// W'[unit][c][b] = 2 scale conj(g_c) W_cb g_b.
-__global__ void build_w_kernel(const float2 *R, const float2 *g, const float2 *M,
-                               const float *scale, float2 *W, int S, int units)
-{
-    const int N = 2 * S;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)units * N * N) return;
-    const int unit = (int)(idx / ((long long)N * N));
-    const int c = (int)((idx / N) % N);
-    const int b = (int)(idx % N);
-    const int sc = c >> 1, pc = c & 1, sb = b >> 1, pb = b & 1;
-    const long long B4 = (long long)S * (S + 1) / 2 * 4;
-    const float2 *Ru = R + unit * B4;
-    const float2 *Mu = M + unit * B4;
-    const float2 *gu = g + (long long)unit * N;
-    float2 w = make_float2(0.f, 0.f);
-    if (sc <= sb) {
-        const float2 e = residual(Ru, gu, Mu, sc, pc, sb, pb);
-        w.x += e.x;
-        w.y += e.y;
+    __shared__ float2 red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[threadIdx.x].x += red[threadIdx.x + h].x;
+            red[threadIdx.x].y += red[threadIdx.x + h].y;
+        }
+        __syncthreads();
     }
-    if (sb <= sc) {
-        const float2 e = residual(Ru, gu, Mu, sb, pb, sc, pc);
-        w.x += e.x;
-        w.y -= e.y;
-    }
-    const float s = 2.f * (scale ? *scale : 1.f);
-    const float2 v = cmul(cmul(cconj(gu[c]), w), gu[b]);
-    W[idx] = make_float2(s * v.x, s * v.y);
+    if (threadIdx.x == 0) grad[(long long)unit * N + c] = make_float2(s * red[0].x, s * red[0].y);
 }
 
 // grad_x[unit][s][t][p] = sum_b W'[unit][(s,p)][b] x[unit][b][t], b = (s', p').
@@ -260,21 +250,22 @@ cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, 
 }
 
 cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
-                             const float *scale, float2 *grad_g, int S, int units,
+                             const float *scale, float2 *grad_g, void *W, int S, int units,
                              cudaStream_t s)
 {
-    const long long n = (long long)units * 2 * S;
-    gain_grad_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(R, g, M, scale, grad_g, S, units);
+    const int N = 2 * S;
+    // threads: a power of two (the reduction halves), up to 256, about N
+    int threads = 32;
+    while (threads < N && threads < 256) threads <<= 1;
+    gain_grad_w_kernel<<<(unsigned)((long long)N * units), threads, 0, s>>>(
+        R, g, M, scale, grad_g, static_cast<float2 *>(W), S);
     return cudaGetLastError();
 }
 
-cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
-                              const float2 *M, const float *scale, float2 *W,
-                              float2 *grad_x, int S, int T, int units, cudaStream_t s)
+cudaError_t input_grad_launch(const float2 *x, const float2 *W, float2 *grad_x, int S, int T, int units,
+                              cudaStream_t s)
 {
     const long long N = 2LL * S;
-    const long long n = (long long)units * N * N;
-    build_w_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, g, M, scale, W, S, units);
     if (T > 0) {
         constexpr int BM = 16 * CORR_IG_TM;
         constexpr size_t smem = (size_t)(2 * 16 * (BM + 2) + 2 * 16 * 64) * sizeof(float2);

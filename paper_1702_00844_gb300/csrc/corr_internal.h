@@ -35,12 +35,14 @@ cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int thr
 // -------------------------------------------------------------- gain adjoint
 cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, float2 *V,
                              float *partial, float *loss, int S, int units, cudaStream_t s);
+// dL/d conj(g); with W (units x 2S x 2S complex64) also the matrix W' of the
+// input gradient, from the same residuals.
 cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
-                             const float *scale, float2 *grad_g, int S, int units,
+                             const float *scale, float2 *grad_g, void *W, int S, int units,
                              cudaStream_t s);
-cudaError_t input_grad_launch(const float2 *x, const float2 *R, const float2 *g,
-                              const float2 *M, const float *scale, float2 *W,
-                              float2 *grad_x, int S, int T, int units, cudaStream_t s);
+// dL/d conj(x) = W' x per channel (W' from gain_grad_launch).
+cudaError_t input_grad_launch(const float2 *x, const float2 *W, float2 *grad_x, int S, int T, int units,
+                              cudaStream_t s);
 
 // ------------------------------------------------------------ layouts
 // Permutes n_integrations x (C x S x T) elements of elem_bytes (4, 8 or 16)

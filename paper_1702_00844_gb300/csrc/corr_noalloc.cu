@@ -97,11 +97,10 @@ extern "C" corr_status_t corr_gain_backward_noalloc(int n_stations, int n_units,
     const float2 *g = static_cast<const float2 *>(d_gain);
     const float2 *M = static_cast<const float2 *>(d_vis_model);
     cudaError_t e = corr::gain_grad_launch(R, g, M, d_grad_scale, static_cast<float2 *>(d_grad_gain),
-                                           n_stations, n_units, s);
+                                           d_grad_in ? W : nullptr, n_stations, n_units, s);
     if (e == cudaSuccess && d_grad_in)
-        e = corr::input_grad_launch(static_cast<const float2 *>(d_in), R, g, M, d_grad_scale, W,
-                                    static_cast<float2 *>(d_grad_in), n_stations, n_samples,
-                                    n_units, s);
+        e = corr::input_grad_launch(static_cast<const float2 *>(d_in), W, static_cast<float2 *>(d_grad_in),
+                                    n_stations, n_samples, n_units, s);
     if (e == cudaSuccess && d_loss)
         e = corr::gain_loss_launch(R, g, M, nullptr, partial, d_loss, n_stations, n_units, s);
     if (e != cudaSuccess) {
