@@ -47,8 +47,9 @@ __global__ void gain_loss_kernel(const float2 *R, const float2 *g, const float2 
     for (long long k = threadIdx.x; k < B4; k += blockDim.x) {
         const long long b = k >> 2;
         const int p1 = (k >> 1) & 1, p2 = k & 1;
-        // invert b = s2(s2+1)/2 + s1
-        int s2 = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        // invert b = s2(s2+1)/2 + s1 (single-precision estimate, then
+        // corrected exactly in integers)
+        int s2 = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
         while ((long long)s2 * (s2 + 1) / 2 > b) --s2;
         while ((long long)(s2 + 1) * (s2 + 2) / 2 <= b) ++s2;
         const int s1 = (int)(b - (long long)s2 * (s2 + 1) / 2);
