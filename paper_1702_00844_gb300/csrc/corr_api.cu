@@ -146,6 +146,7 @@ void fp32_config(corr_plan *h)
     h->fp_threads = ((p.group_size + 31) / 32) * 32;
     const int nbox = (S + 7) / 8;
     int tc = 32;
+    if (const char *e = std::getenv("CORR_FP32_TC")) tc = std::max(1, std::min(64, std::atoi(e)));
     while (tc > 1 && (size_t)FP32_STAGES * nbox * tc * 128 > 100 * 1024) tc >>= 1;
     p.tc = tc;
     h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;

@@ -27,7 +27,10 @@ struct Fp32Params {
     int ksplit, kchunks;
     float2 *partial;
 };
-constexpr int FP32_STAGES = 3;
+#ifndef CORR_FP32_STAGES
+#define CORR_FP32_STAGES 3
+#endif
+constexpr int FP32_STAGES = CORR_FP32_STAGES;
 // npol 2: samples through the TMA map tmap; npol 1: through p.in1.
 cudaError_t fp32_launch(const void *tmap, const Fp32Params &p, int npol, int threads, size_t smem,
                         cudaStream_t s);
