@@ -151,14 +151,22 @@ void fp32_config(corr_plan *h)
     p.tc = tc;
     h->fp_smem = (size_t)FP32_STAGES * nbox * tc * 128 + 128;
     // Few units (channels x integrations) leave SMs idle: then the sample
-    // axis is split into ranges of whole chunks over more CTAs (about two per
-    // SM), and a second kernel sums the partial results in order.
+    // axis is split into ranges of whole chunks over more CTAs, and a second
+    // kernel sums the partial results in order.
     // CORR_FP32_KSPLIT forces a split count.
+    // Both sub-tile forms fit two CTAs per SM. Measured on 64 channels of 64
+    // stations, many short CTAs run best (16 CTAs of 2 chunks per channel:
+    // 0.144 ms against 0.159 for 4 of 8 and 0.175 for 5 of 7): chunks per
+    // CTA are chosen for about four waves of 2 x SMs CTAs, at least 2.
     const int total = std::max(1, (p.T + tc - 1) / tc);
     const long long ctas = (long long)p.n_units * p.groups;
+    const long long slots = 2LL * h->sm_count;
     int ks = 1;
-    if (p.T > 0 && ctas < 2LL * h->sm_count)
-        ks = (int)std::min<long long>(total, (2LL * h->sm_count + ctas - 1) / ctas);
+    if (p.T > 0 && total > 1 && ctas < slots) {
+        const long long per = std::min<long long>(
+            total, std::max<long long>(2, ((long long)total * ctas + 4 * slots - 1) / (4 * slots)));
+        ks = (int)((total + per - 1) / per);
+    }
     if (const char *e = std::getenv("CORR_FP32_KSPLIT")) ks = std::max(1, std::min(total, std::atoi(e)));
     p.kchunks = (total + ks - 1) / ks;
     p.ksplit = (total + p.kchunks - 1) / p.kchunks;

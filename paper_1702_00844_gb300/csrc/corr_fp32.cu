@@ -115,10 +115,12 @@ __device__ __noinline__ void stage_single_pol(uint32_t base, const float2 *in1u,
 }
 
 // TW = 4: 4 x 4-station sub-tiles (128 accumulators, 168 registers, CTAs of
-// at most 192 threads); TW = 2: 4 x 2 (64 accumulators, 112 registers, CTAs of
-// at most 288 threads), more warps per SM for the same shared memory.
+// at most 192 threads); TW = 2: 4 x 2 (64 accumulators, 96 registers, CTAs of
+// at most 288 threads). A warp's registers come from one SM sub-partition's
+// 64 KB file: 168 registers allow 3 warps per sub-partition (two 5-warp
+// CTAs), 96 allow 5 (two 9-warp CTAs).
 template <int NPOL, int TW>
-__global__ void __maxnreg__(TW == 4 ? 168 : 112) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                        const Fp32Params p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -339,6 +341,11 @@ cudaError_t launch_tw(const void *tmap, const Fp32Params &p, int threads, size_t
     const unsigned grid = (unsigned)(p.n_units * p.groups * p.ksplit);
     cudaError_t e = cudaFuncSetAttribute(fp32_correlate_kernel<NPOL, TW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1/shared array as shared memory, so that two CTAs'
+    // stages fit an SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fp32_correlate_kernel<NPOL, TW>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (NPOL == 1) {
         CUtensorMap unused{};
