@@ -144,6 +144,7 @@ void fp32_config(corr_plan *h)
     p.groups = (p.nsub + max_threads - 1) / max_threads;
     p.group_size = (p.nsub + p.groups - 1) / p.groups;
     h->fp_threads = ((p.group_size + 31) / 32) * 32;
+    if (p.tw == 2 && h->d.n_pols == 2) h->fp_threads += 32;   // the load warp of the 4 x 2 form
     const int nbox = (S + 7) / 8;
     int tc = 32;
     if (const char *e = std::getenv("CORR_FP32_TC")) tc = std::max(1, std::min(64, std::atoi(e)));

@@ -127,8 +127,15 @@ __global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __gr
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ uint64_t full[FP32_STAGES];
+    __shared__ uint64_t empty[FP32_STAGES];
     __shared__ int abort_flag;
 
+    // 4 x 2 sub-tiles with TMA staging: one extra warp (the last) issues the
+    // loads, and each compute warp releases a stage on its own (one arrival
+    // per warp on the stage's "empty" barrier), so warps meet no block
+    // barrier per stage and can drift apart by up to FP32_STAGES - 1 stages.
+    constexpr bool PW = NPOL == 2 && TW == 2;
+    const int ncomp = PW ? (int)blockDim.x - 32 : (int)blockDim.x;
     const int tid = threadIdx.x;
     const int grp = blockIdx.x % p.groups;
     const int unit = (blockIdx.x / p.groups) % p.n_units;
@@ -151,7 +158,10 @@ __global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __gr
 
     if (tid == 0) {
         if (NPOL == 2) prefetch_tmap(&tmap);
-        for (int s = 0; s < FP32_STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < FP32_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], (uint32_t)(ncomp / 32));
+        }
         abort_flag = 0;
         fence_mbar_init();
     }
@@ -174,8 +184,27 @@ __global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __gr
     };
     if (NPOL == 1) {
         for (int kc = 0; kc < FP32_STAGES; ++kc) issue1(kc);
-    } else if (tid == 0) {
+    } else if (!PW && tid == 0) {
         for (int kc = 0; kc < FP32_STAGES && kc < nchunks; ++kc) issue(kc);
+    }
+    if (PW && tid >= ncomp) {
+        // the load warp: refills stage kc % FP32_STAGES once every compute
+        // warp has released its previous use
+        if (tid == ncomp) {
+            int issued = 0;
+            for (int kc = 0; kc < nchunks; ++kc) {
+                const int st = kc % FP32_STAGES;
+                if (kc >= FP32_STAGES &&
+                    !mbar_wait_bounded(&empty[st], ((kc / FP32_STAGES) - 1) & 1, &abort_flag, p.err, p.wait_ns))
+                    break;
+                issue(kc);
+                ++issued;
+            }
+            // on a give-up, let the loads in flight land before the CTA (and
+            // its shared memory) goes away; fixed 2 s bound per stage
+            if (abort_flag) drain_issued(full, max(0, issued - FP32_STAGES), issued, p.err);
+        }
+        return;
     }
 
     int row_off[4], col_off[TW];
@@ -249,6 +278,12 @@ __global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __gr
                             fma2(acc[a][b][2 * pp], acc[a][b][2 * pp + 1], R2[a][pp >> 1], C2[b][pp & 1]);
                         }
             }
+        }
+        if (PW) {
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+            if (!ok || abort_flag) break;
+            continue;
         }
         __syncthreads();
         if (NPOL == 1) {
