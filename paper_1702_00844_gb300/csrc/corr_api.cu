@@ -139,12 +139,17 @@ void fp32_config(corr_plan *h)
     for (int i = 0; i < p.nq; ++i) p.nsub += p.ncq - 4 * i / p.tw;
     // at most 192 threads per CTA (4 x 4: two CTAs of 168-register threads
     // fit an SM) or 288 (4 x 2: two CTAs of 112-register threads)
+    // A load warp (two pols, TMA staging) replaces the block barrier per
+    // stage in the 4 x 2 form. (Measured in the 4 x 4 form, where it takes
+    // the place of a sixth compute warp: slower at 128 and 256 stations,
+    // faster at 512.)
+    p.load_warp = h->d.n_pols == 2 && p.tw == 2 ? 1 : 0;
     int max_threads = p.tw == 4 ? 192 : 288;
     if (const char *e = std::getenv("CORR_FP32_MAXT")) max_threads = std::max(32, std::min(max_threads, std::atoi(e)));
     p.groups = (p.nsub + max_threads - 1) / max_threads;
     p.group_size = (p.nsub + p.groups - 1) / p.groups;
     h->fp_threads = ((p.group_size + 31) / 32) * 32;
-    if (p.tw == 2 && h->d.n_pols == 2) h->fp_threads += 32;   // the load warp of the 4 x 2 form
+    if (p.load_warp) h->fp_threads += 32;
     const int nbox = (S + 7) / 8;
     int tc = 32;
     if (const char *e = std::getenv("CORR_FP32_TC")) tc = std::max(1, std::min(64, std::atoi(e)));

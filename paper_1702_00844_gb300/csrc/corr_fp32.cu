@@ -130,11 +130,11 @@ __global__ void __maxnreg__(TW == 4 ? 168 : 96) fp32_correlate_kernel(const __gr
     __shared__ uint64_t empty[FP32_STAGES];
     __shared__ int abort_flag;
 
-    // 4 x 2 sub-tiles with TMA staging: one extra warp (the last) issues the
+    // With TMA staging and p.load_warp: one extra warp (the last) issues the
     // loads, and each compute warp releases a stage on its own (one arrival
     // per warp on the stage's "empty" barrier), so warps meet no block
     // barrier per stage and can drift apart by up to FP32_STAGES - 1 stages.
-    constexpr bool PW = NPOL == 2 && TW == 2;
+    const bool PW = NPOL == 2 && TW == 2 && p.load_warp;
     const int ncomp = PW ? (int)blockDim.x - 32 : (int)blockDim.x;
     const int tid = threadIdx.x;
     const int grp = blockIdx.x % p.groups;

@@ -12,6 +12,7 @@ struct Fp32Params {
     float2 *out;
     int S, T, n_units;                // S: (pseudo-)stations of the sub-tile grid
     int tw;                           // sub-tiles of 4 x tw stations (tw = 4 or 2)
+    int load_warp;                    // 1: an extra warp issues the TMA loads (two pols only)
     int nq, ncq;                      // row groups (4 stations) and column groups (tw)
     int nsub, groups, group_size;     // sub-tiles per unit and their grouping over CTAs
     int tc;                           // samples per pipeline stage
