@@ -206,6 +206,17 @@ corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_
  * a cluster of two such CTAs cannot be resident). */
 int corr_tile_variant(corr_handle_t h);
 
+/* Measurement hook: with two CUDA events (cudaEvent_t passed as void*), every
+ * later corr_correlate / corr_correlate_host chunk on this plan records
+ * ev_start on its stream right before the launch of the plan's main kernel
+ * (tensor path: the first launch over its main tile list, i.e. the
+ * power-checked launch of int8, not the redo or tail launches; FP32 path:
+ * the correlation kernel and, for a split sample axis, its reduction) and
+ * ev_stop right after it, so cudaEventElapsedTime gives that kernel's
+ * duration. The plan does not own the events; NULL, NULL turns the hook off.
+ * CORR_ERR_INVALID_ARG if only one is NULL. */
+corr_status_t corr_set_kernel_events(corr_handle_t h, void *ev_start, void *ev_stop);
+
 /* Tile variant of the plan's current ragged batch (same codes as
  * corr_tile_variant), chosen on the first corr_correlate_batched call with
  * that set of sub-arrays; -1 before any batch or for NULL. */

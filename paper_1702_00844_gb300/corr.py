@@ -74,6 +74,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_tile_variant.restype = ip
     L.corr_batch_tile_variant.argtypes = [vp]
     L.corr_batch_tile_variant.restype = ip
+    L.corr_set_kernel_events.argtypes = [vp, vp, vp]
+    L.corr_set_kernel_events.restype = ip
     L.corr_tc_tiles.argtypes = [ip]
     L.corr_tc_tile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_fp32_subtiles.argtypes = [ip]
@@ -236,6 +238,14 @@ class Plan:
     def tile_variant(self) -> str:
         v = self.L.corr_tile_variant(self.h)
         return {0: "narrow", 1: "wide", 2: "pair"}.get(v, "fp32")
+
+    def set_kernel_events(self, start=None, stop=None):
+        """``corr_set_kernel_events``: record ``start``/``stop``
+        (torch.cuda.Event, already created on the device) around the plan's
+        main kernel launch in later calls; no arguments turn it off."""
+        a = start._as_parameter_ if start is not None else None
+        b = stop._as_parameter_ if stop is not None else None
+        _check(self.L.corr_set_kernel_events(self.h, a, b), "corr_set_kernel_events")
 
     def batch_tile_variant(self) -> Optional[str]:
         """Tile variant of the current ragged batch (None before any)."""

@@ -74,3 +74,39 @@ def test_tensor_and_fp32_plans_on_concurrent_streams():
     ref = oracle.correlate(xc)
     got = o32.cpu().numpy().reshape(ref.shape)
     assert rel_frobenius_per_unit(got, ref).max() < TOL_FP32
+
+
+@pytest.mark.parametrize("dtype,path", [("ci8", "tensor"), ("cf32", "fp32")])
+def test_kernel_event_hook_brackets_the_main_launch(dtype, path):
+    """corr_set_kernel_events: the events bracket the plan's main kernel,
+    whose duration is positive and below that of the whole call (int8: the
+    redo launch and its memsets stay outside); results are unchanged."""
+    from paper_1702_00844_gb300 import Plan
+    S, C, T = 256, 32, 1024
+    g = synth.rng(73)
+    if dtype == "ci8":
+        x = synth.int8_normal(g, (C, S, T, 2))
+    else:
+        x = synth.complex_normal(g, (C, S, T, 2)).astype(np.complex64)
+    plan = Plan(S, C, T, dtype=dtype, path=path)
+    xd = torch.from_numpy(x).cuda()
+    out = plan.empty_out()
+    plan.correlate(xd, out)
+    ka, kb, ca, cb = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    for e in (ka, kb):
+        e.record()
+    torch.cuda.synchronize()
+    plan.set_kernel_events(ka, kb)
+    ca.record()
+    plan.correlate(xd, out)
+    cb.record()
+    plan.set_kernel_events()
+    torch.cuda.synchronize()
+    plan.check_error()
+    k_ms, c_ms = ka.elapsed_time(kb), ca.elapsed_time(cb)
+    assert 0 < k_ms <= c_ms
+    if dtype == "ci8":
+        exact(out, x)
+    else:
+        ref = oracle.correlate(x)
+        assert rel_frobenius_per_unit(out.cpu().numpy().reshape(ref.shape), ref).max() < TOL_FP32
