@@ -41,7 +41,6 @@ struct corr_plan {
     // int8 power check / redo list (single problem and batches)
     int *d_redo_mark = nullptr;
     int4 *d_redo_items = nullptr;
-    int *d_redo_count = nullptr;
     int redo_cap = 0;
     // ragged batches
     std::vector<corr_subarray_t> batch_key;
@@ -264,8 +263,10 @@ corr_status_t ensure_redo(corr_plan *h, int n)
     h->d_redo_items = nullptr;
     h->redo_cap = 0;
     corr_status_t st;
-    if (!h->d_redo_count && (st = cuda_status(cudaMalloc(&h->d_redo_count, 2 * sizeof(int)))) != CORR_OK) return st;
-    if ((st = cuda_status(cudaMalloc(&h->d_redo_mark, (size_t)n * sizeof(int)))) != CORR_OK) return st;
+    // per item list (ctr 0 and 1) its counter directly followed by its marks,
+    // so that one memset clears both: list (redo_off, ctr) uses entries
+    // redo_off + ctr (counter) and redo_off + ctr + 1 ... (marks)
+    if ((st = cuda_status(cudaMalloc(&h->d_redo_mark, ((size_t)n + 2) * sizeof(int)))) != CORR_OK) return st;
     if ((st = cuda_status(cudaMalloc(&h->d_redo_items, (size_t)n * sizeof(int4)))) != CORR_OK) return st;
     h->redo_cap = n;
     return CORR_OK;
@@ -304,16 +305,15 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
         if (mark) cudaEventRecord(h->ev_k1, s);
         return st;
     }
-    corr_status_t st =
-        cuda_status(cudaMemsetAsync(h->d_redo_mark + redo_off, 0, (size_t)p.n_items * sizeof(int), s));
-    if (st == CORR_OK) st = cuda_status(cudaMemsetAsync(h->d_redo_count + ctr, 0, sizeof(int), s));
+    int *count = h->d_redo_mark + redo_off + ctr;
+    corr_status_t st = cuda_status(cudaMemsetAsync(count, 0, ((size_t)p.n_items + 1) * sizeof(int), s));
     if (st != CORR_OK) return st;
     TcParams a = p;
     a.chunk_kb = 0;
     a.check_power = 1;
-    a.redo_mark = h->d_redo_mark + redo_off;
+    a.redo_mark = count + 1;
     a.redo_items = h->d_redo_items + redo_off;
-    a.redo_count = h->d_redo_count + ctr;
+    a.redo_count = count;
     if (mark) cudaEventRecord(h->ev_k0, s);
     st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
     if (mark) cudaEventRecord(h->ev_k1, s);
@@ -321,7 +321,7 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
     TcParams b = p;
     b.items = h->d_redo_items + redo_off;
     b.n_items = p.n_items;          // upper bound; the count is read on the device
-    b.n_items_dev = h->d_redo_count + ctr;
+    b.n_items_dev = count;
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
     return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s));
@@ -1024,7 +1024,6 @@ corr_status_t corr_destroy(corr_handle_t h)
     cudaFree(h->d_items);
     cudaFree(h->d_redo_mark);
     cudaFree(h->d_redo_items);
-    cudaFree(h->d_redo_count);
     cudaFree(h->d_bprobs);
     cudaFree(h->d_bitems);
     for (int b = 0; b < 2; ++b) {
