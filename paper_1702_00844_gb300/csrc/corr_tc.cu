@@ -419,6 +419,16 @@ __device__ __forceinline__ TcProblem get_prob(const TcParams &p, int k)
     return p.probs ? p.probs[k] : p.prob0;
 }
 
+// MMA width N of a narrow tile: the rows of its column block that hold
+// stations (2 per station with two pols, 1 per station with one), rounded
+// up to a multiple of 16. A partial last block (S not a multiple of the
+// block) is then not multiplied in full.
+template <int NPOL> __device__ __forceinline__ int narrow_n(int S, int cb)
+{
+    const int rows = NPOL == 2 ? 2 * min(TC_RS, S - cb * TC_RS) : min(2 * TC_RS, S - cb * 2 * TC_RS);
+    return (rows + 15) & ~15;
+}
+
 __device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
 {
     return chunk_kb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
@@ -747,7 +757,9 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
             // NPOL = 1: the row's station; NPOL = 2: its station (pol p1)
             const int s1 = NPOL == 1 ? (item.rb + (int)rank) * 2 * TC_RS + row
                                      : (item.rb + (int)rank) * TC_RS + sl;
-            const int ngroups = 8 * item.ncb;  // groups of 8 column (pseudo-)stations
+            // groups of 8 column (pseudo-)stations; a narrow tile reads the
+            // columns its MMAs wrote (narrow_n)
+            const int ngroups = V == TC_NARROW ? narrow_n<NPOL>(P.S, item.cb0) / 16 : 8 * item.ncb;
             const long long unit_off = (long long)item.unit * P.out_unit_elems + (NPOL == 1 ? 0 : p1 * 2);
             for (int c = 0; c < nch; ++c, ++acc_it) {
                 const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
@@ -827,8 +839,13 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
             const TcProblem P = get_prob(p, item.prob);
             const bool diag = item.cb0 == item.rb;
             const bool n256 = N256 && item.ncb == 2;
-            const uint32_t idesc = n256 ? ID256 : ID128;
-            const uint32_t idesc_neg = n256 ? ID256N : ID128N;
+            uint32_t idesc = n256 ? ID256 : ID128;
+            uint32_t idesc_neg = n256 ? ID256N : ID128N;
+            if constexpr (V == TC_NARROW) {
+                const int n = narrow_n<NPOL>(P.S, item.cb0);   // 16 .. 128, a multiple of 16
+                idesc = idesc_f16_f32(M, n, false);
+                idesc_neg = idesc_f16_f32(M, n, true);
+            }
             const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
             const int nch = n_chunks(nkb, p.chunk_kb);
             const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
