@@ -419,10 +419,10 @@ __device__ __forceinline__ TcProblem get_prob(const TcParams &p, int k)
     return p.probs ? p.probs[k] : p.prob0;
 }
 
-// MMA width N of a narrow tile: the rows of its column block that hold
-// stations (2 per station with two pols, 1 per station with one), rounded
-// up to a multiple of 16. A partial last block (S not a multiple of the
-// block) is then not multiplied in full.
+// MMA rows of column block cb that hold stations (2 per station with two
+// pols, 1 per station with one), rounded up to a multiple of 16: a partial
+// last block (S not a multiple of the block) is not multiplied in full by
+// narrow and wide tiles.
 template <int NPOL> __device__ __forceinline__ int narrow_n(int S, int cb)
 {
     const int rows = NPOL == 2 ? 2 * min(TC_RS, S - cb * TC_RS) : min(2 * TC_RS, S - cb * 2 * TC_RS);
@@ -757,9 +757,10 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
             // NPOL = 1: the row's station; NPOL = 2: its station (pol p1)
             const int s1 = NPOL == 1 ? (item.rb + (int)rank) * 2 * TC_RS + row
                                      : (item.rb + (int)rank) * TC_RS + sl;
-            // groups of 8 column (pseudo-)stations; a narrow tile reads the
-            // columns its MMAs wrote (narrow_n)
-            const int ngroups = V == TC_NARROW ? narrow_n<NPOL>(P.S, item.cb0) / 16 : 8 * item.ncb;
+            // groups of 8 column (pseudo-)stations; narrow and wide tiles
+            // read the columns their MMAs wrote (narrow_n)
+            const int ngroups = PAIR ? 8 * item.ncb
+                                     : ((item.ncb - 1) * 128 + narrow_n<NPOL>(P.S, item.cb0 + item.ncb - 1)) / 16;
             const long long unit_off = (long long)item.unit * P.out_unit_elems + (NPOL == 1 ? 0 : p1 * 2);
             for (int c = 0; c < nch; ++c, ++acc_it) {
                 const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
@@ -841,8 +842,10 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
             const bool n256 = N256 && item.ncb == 2;
             uint32_t idesc = n256 ? ID256 : ID128;
             uint32_t idesc_neg = n256 ? ID256N : ID128N;
-            if constexpr (V == TC_NARROW) {
-                const int n = narrow_n<NPOL>(P.S, item.cb0);   // 16 .. 128, a multiple of 16
+            if constexpr (!PAIR) {
+                // full column blocks, then the last one's rows with stations:
+                // 16 .. 256, a multiple of 16
+                const int n = (item.ncb - 1) * 128 + narrow_n<NPOL>(P.S, item.cb0 + item.ncb - 1);
                 idesc = idesc_f16_f32(M, n, false);
                 idesc_neg = idesc_f16_f32(M, n, true);
             }
