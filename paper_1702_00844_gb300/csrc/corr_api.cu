@@ -661,12 +661,17 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
         }
         if (d.flags & CORR_FLAG_HOST_IO) {
             // chunks of about 32 MiB of input (CORR_HOST_CHUNK_MB overrides;
-            // at least one channel)
+            // at least one channel), and on the FP32 path at least one full
+            // wave of its CTAs (two per SM, `groups` per channel): each chunk
+            // is its own launch, and a FP32 CTA takes one channel, so small
+            // channels would leave most SMs idle
             size_t chunk_mb = 32;
             if (const char *e = std::getenv("CORR_HOST_CHUNK_MB")) chunk_mb = std::max(1ul, std::strtoul(e, nullptr, 10));
             const size_t ub = std::max<size_t>(1, in_unit_bytes(d));
-            h->chunk_units = (int)std::max<long long>(
-                1, std::min<long long>(units, (long long)((chunk_mb << 20) / ub)));
+            long long cu = (long long)((chunk_mb << 20) / ub);
+            if (h->path == CORR_PATH_FP32)
+                cu = std::max<long long>(cu, (2LL * h->sm_count + h->fp.groups - 1) / h->fp.groups);
+            h->chunk_units = (int)std::max<long long>(1, std::min<long long>(units, cu));
             const size_t ib = (size_t)h->chunk_units * in_unit_bytes(d);
             const size_t ob = (size_t)h->chunk_units * out_unit_bytes(d);
             for (int b = 0; b < 2 && st == CORR_OK; ++b) {
