@@ -13,9 +13,9 @@
 //
 // Registers are capped at 168 per thread and CTAs at 192 threads so that two
 // CTAs share an SM (at most 3 warps per SM sub-partition). Up to 64 stations
-// the sub-tiles are 4 x 2 stations instead (64 accumulators, 112 registers,
-// CTAs of up to 288 threads): the same FMAs per accumulator in the same
-// order, on more threads.
+// the sub-tiles are 4 x 2 stations instead (64 accumulators, 96 registers,
+// CTAs of up to 288 compute threads plus one warp that only issues the TMA
+// loads): the same FMAs per accumulator in the same order, on more threads.
 //
 // One polarisation (NPOL = 1): stations 2m and 2m+1 act as the two pols of
 // pseudo-station m. A box of 16 stations x tc samples of 8-byte complex
