@@ -278,7 +278,9 @@ int corr_tc_tile_decode(int n_stations, int k, int *rb, int *cb);
 
 /* Number of 4x4-station register tiles of the FP32 path per channel
  * (upper triangle, diagonal included) and the decode of tile k into its
- * row and column index (i <= j). Returns -1 for k out of range. */
+ * row and column index (i <= j). Returns -1 for k out of range. The FP32
+ * kernel uses this map above 64 stations; up to 64 it uses 4x2-station
+ * tiles, row i holding column pairs j = 2i .. ceil(S/2) - 1. */
 int corr_fp32_subtiles(int n_stations);
 int corr_fp32_subtile_decode(int n_stations, int k, int *i, int *j);
 
