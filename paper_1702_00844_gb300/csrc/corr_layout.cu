@@ -87,17 +87,23 @@ __global__ void __launch_bounds__(RTHREADS) reorder_vec_kernel(const E *__restri
     const int n_st = (S + TILE - 1) / TILE, n_tt = (T + TILE - 1) / TILE;
     const bool in_s_fast = from == CORR_LAYOUT_CTS, out_s_fast = to == CORR_LAYOUT_CTS;
     const long long per_integration = (long long)S * C * T;
-    for (long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    // tile k -> (integration base, channel c, first station s0, first time t0)
+    auto tile_of = [&](long long k, long long &base, int &c, int &s0, int &t0) {
         const int tt = (int)(k % n_tt);
         long long r = k / n_tt;
         const int st = (int)(r % n_st);
         r /= n_st;
-        const int c = (int)(r % C);
-        const long long base = (r / C) * per_integration;
-        const int s0 = st * TILE, t0 = tt * TILE;
-        uint4 buf[PER];
+        c = (int)(r % C);
+        base = (r / C) * per_integration;
+        s0 = st * TILE;
+        t0 = tt * TILE;
+    };
+    auto load = [&](long long k, uint4 (&buf)[PER]) {
+        long long base;
+        int c, s0, t0;
+        tile_of(k, base, c, s0, t0);
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {      // all loads first: PER x 16 bytes in flight per thread
+        for (int j = 0; j < PER; ++j) {
             const int id = threadIdx.x + j * RTHREADS;
             const int v = id % NV, row = id / NV;
             const int s = s0 + (in_s_fast ? v * V : row);
@@ -106,11 +112,21 @@ __global__ void __launch_bounds__(RTHREADS) reorder_vec_kernel(const E *__restri
                          ? __ldg(reinterpret_cast<const uint4 *>(in + base + layout_offset(from, S, C, T, c, s, t)))
                          : make_uint4(0, 0, 0, 0);
         }
+    };
+    // The loads of the CTA's next tile are issued before the stores of the
+    // current one, so that both are in flight together.
+    uint4 cur[PER], nxt[PER];
+    long long k = blockIdx.x;
+    if (k < n_tiles) load(k, cur);
+    for (; k < n_tiles; k += gridDim.x) {
+        long long base;
+        int c, s0, t0;
+        tile_of(k, base, c, s0, t0);
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const int id = threadIdx.x + j * RTHREADS;
             const int v = id % NV, row = id / NV;
-            const E *e = reinterpret_cast<const E *>(&buf[j]);
+            const E *e = reinterpret_cast<const E *>(&cur[j]);
 #pragma unroll
             for (int q = 0; q < V; ++q) {
                 if (in_s_fast)
@@ -120,6 +136,7 @@ __global__ void __launch_bounds__(RTHREADS) reorder_vec_kernel(const E *__restri
             }
         }
         __syncthreads();
+        if (k + gridDim.x < n_tiles) load(k + gridDim.x, nxt);
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const int id = threadIdx.x + j * RTHREADS;
@@ -136,6 +153,8 @@ __global__ void __launch_bounds__(RTHREADS) reorder_vec_kernel(const E *__restri
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) cur[j] = nxt[j];
     }
 }
 
