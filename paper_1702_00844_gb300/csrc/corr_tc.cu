@@ -125,6 +125,30 @@ template <> struct Cfg<2, TC_PAIR> {
 };
 #endif
 
+// int8 pair tiles of two pols stage the epilogue's last column groups in
+// shared memory: STG groups of 8 column stations (4 KB per epilogue warp),
+// copied there raw from TMEM so that the accumulator is released sooner;
+// their conversion and global stores follow while the next tile's MMAs run.
+// The operand ring is one stage shorter to make room. Measured on 256
+// stations: 4 operand stages + 6 staged groups 1-1.5% faster than 6 stages
+// without staging (3 + 8: equal; f16 pair tiles: slower, so STG = 0 there).
+#ifndef CORR_TC_OPS_STG_I8
+#define CORR_TC_OPS_STG_I8 4
+#endif
+#ifndef CORR_TC_STG_I8
+#define CORR_TC_STG_I8 6
+#endif
+constexpr int STG_GROUP_BYTES = 8 * 512;  // per warp: 8 column stations x 32 rows x 16 B
+
+// Stage counts per (input type, tile variant, pols): OPS operand stages, RAW
+// raw-sample stages, STG staged epilogue groups per epilogue warp.
+template <int DT, int V, int NPOL> struct Lay {
+    static constexpr bool STAGED = V == TC_PAIR && NPOL == 2 && DT == 2 && CORR_TC_STG_I8 > 0;
+    static constexpr int STG = STAGED ? CORR_TC_STG_I8 : 0;
+    static constexpr int OPS = STAGED ? CORR_TC_OPS_STG_I8 : Cfg<DT, V>::OPS;
+    static constexpr int RAW = Cfg<DT, V>::RAW;
+};
+
 template <int DT, int V> __host__ __device__ constexpr int stage_bytes()
 {
     return (1 + Cfg<DT, V>::MAXB) * TILE_BYTES;
@@ -133,9 +157,11 @@ template <int DT, int V> __host__ __device__ constexpr int raw_stage_bytes()
 {
     return (1 + Cfg<DT, V>::MAXB) * RawBytes<DT>::value * N_PRODUCERS;
 }
-template <int DT, int V> __host__ __device__ constexpr int smem_bytes()
+template <int DT, int V, int NPOL> __host__ __device__ constexpr int smem_bytes()
 {
-    return Cfg<DT, V>::OPS * stage_bytes<DT, V>() + Cfg<DT, V>::RAW * raw_stage_bytes<DT, V>();
+    using L = Lay<DT, V, NPOL>;
+    return L::OPS * stage_bytes<DT, V>() + L::RAW * raw_stage_bytes<DT, V>() +
+           L::STG * 4 * STG_GROUP_BYTES;
 }
 
 struct Bars {
@@ -148,15 +174,19 @@ struct Bars {
     int abort_flag;
 };
 
-template <int DT, int V> constexpr bool cfg_ok()
+template <int DT, int V, int NPOL> constexpr bool cfg_ok()
 {
-    return Cfg<DT, V>::OPS >= 2 && Cfg<DT, V>::OPS <= MAX_OPS &&
-           (Cfg<DT, V>::RAW >= 2 || (Cfg<DT, V>::RAW == 0 && DT == 2)) &&
-           smem_bytes<DT, V>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
+    using L = Lay<DT, V, NPOL>;
+    return L::OPS >= 2 && L::OPS <= MAX_OPS && (L::RAW >= 2 || (L::RAW == 0 && DT == 2)) &&
+           L::STG >= 0 && L::STG <= 16 &&
+           smem_bytes<DT, V, NPOL>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
 }
-static_assert(cfg_ok<1, TC_NARROW>() && cfg_ok<2, TC_NARROW>() && cfg_ok<1, TC_WIDE>() &&
-                  cfg_ok<2, TC_WIDE>() && cfg_ok<1, TC_PAIR>() && cfg_ok<2, TC_PAIR>(),
-              "stage counts must fit the barrier arrays and shared memory");
+template <int DT> constexpr bool cfg_ok_dt()
+{
+    return cfg_ok<DT, TC_NARROW, 1>() && cfg_ok<DT, TC_NARROW, 2>() && cfg_ok<DT, TC_WIDE, 1>() &&
+           cfg_ok<DT, TC_WIDE, 2>() && cfg_ok<DT, TC_PAIR, 1>() && cfg_ok<DT, TC_PAIR, 2>();
+}
+static_assert(cfg_ok_dt<1>() && cfg_ok_dt<2>(), "stage counts must fit the barrier arrays and shared memory");
 
 template <int DT> struct Raw;          // raw samples of 8 times of one station
 template <> struct Raw<1> { uint4 v[4]; }; // complex f16 x 2 pols: 64 bytes
@@ -528,10 +558,12 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
 template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
 {
     using C = Cfg<DT, V>;
+    using L = Lay<DT, V, NPOL>;
     constexpr bool PAIR = V == TC_PAIR;
     constexpr bool N256 = V != TC_NARROW;          // tiles of two column blocks
-    constexpr int OPS = C::OPS;
-    constexpr int RAW = C::RAW;
+    constexpr int OPS = L::OPS;
+    constexpr int RAW = L::RAW;
+    constexpr int STG = L::STG;
     constexpr int NBUF = C::NBUF;
     constexpr uint32_t STAGE = stage_bytes<DT, V>();
     constexpr uint32_t IMOFF = N256 ? 256 : 128;   // TMEM column of Im relative to Re
@@ -542,7 +574,7 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t tiles_u32 = smem_u32(smem);
     const uint32_t raw_base = tiles_u32 + OPS * STAGE;
-    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, V>());
+    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, V, NPOL>());
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x;
@@ -747,6 +779,9 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
         const int row = eq * 32 + lane;     // A row = 2*station + pol
         const int sl = row >> 1;
         const int p1 = row & 1;
+        // this warp's ring of STG staged groups: group slot k at k * 4 KB,
+        // column station j of it at j * 512 B, one thread's row at lane * 16 B
+        const uint32_t stg_base = raw_base + RAW * raw_stage_bytes<DT, V>() + eq * STG * STG_GROUP_BYTES;
         uint32_t acc_it = 0;
         bool ok = true;
         for (int it = item0; it < n_items && ok; it += item_step) {
@@ -772,37 +807,111 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
                 const uint32_t taddr = tmem_base + buf * BUFCOLS + ((uint32_t)(eq * 32) << 16);
                 const bool last = c == nch - 1;
                 // Column groups of 16 TMEM columns (8 column stations x 2 pols),
-                // Re and Im; the load of the next group overlaps the stores of
-                // the current one (two register sets). The accumulator is
-                // released as soon as its last columns are in registers, so the
-                // last group's stores overlap the next MMAs.
+                // Re and Im. The first ndirect groups are stored to global
+                // memory from registers; the load of the next group overlaps
+                // the stores of the current one (two register sets). The last
+                // nst groups (int8 pair tiles of two pols, one chunk) are
+                // staged in this warp's shared-memory ring, so that the
+                // accumulator is released once they are there; their global
+                // writes then overlap the next tile's MMAs.
+                const int nst = (STG > 0 && nch == 1) ? min(STG, ngroups) : 0;
+                const int ndirect = ngroups - nst;
                 uint32_t ra[16], ia[16], rb2[16], ib2[16];
-                tmem_ld_32x32b_x16(taddr, ra);
-                tmem_ld_32x32b_x16(taddr + IMOFF, ia);
-                tmem_wait_ld();
                 bool released = false;
+                if (ndirect > 0) {
+                    tmem_ld_32x32b_x16(taddr, ra);
+                    tmem_ld_32x32b_x16(taddr + IMOFF, ia);
+                    tmem_wait_ld();
+                }
 #pragma unroll 1
-                for (int cc = 0; cc < ngroups; cc += 2) {
-                    const bool has1 = cc + 1 < ngroups;
+                for (int cc = 0; cc < ndirect; cc += 2) {
+                    const bool has1 = cc + 1 < ndirect;
                     if (has1) {
                         tmem_ld_32x32b_x16(taddr + (cc + 1) * 16, rb2);
                         tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 1) * 16, ib2);
                     }
                     store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
                     tmem_wait_ld();
-                    if (cc + 2 >= ngroups) {  // every column of this chunk has been read
+                    if (nst == 0 && cc + 2 >= ndirect) {  // every column of this chunk has been read
                         tc_fence_before();
                         mbar_arrive(&bars->acc_empty[buf]);
                         released = true;
                     }
                     if (has1) {
-                        if (cc + 2 < ngroups) {
+                        if (cc + 2 < ndirect) {
                             tmem_ld_32x32b_x16(taddr + (cc + 2) * 16, ra);
                             tmem_ld_32x32b_x16(taddr + IMOFF + (cc + 2) * 16, ia);
                         }
                         store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + (cc + 1) * 8, c > 0, last,
-                                        rb2, ib2);
-                        if (cc + 2 < ngroups) tmem_wait_ld();
+                                              rb2, ib2);
+                        if (cc + 2 < ndirect) tmem_wait_ld();
+                    }
+                }
+                if constexpr (STG > 0) {
+                    if (nst > 0) {
+                        // Staged groups: each thread copies its row's raw
+                        // accumulator values to its own 16-byte slots of this
+                        // warp's ring (conflict-free: a warp writes 512
+                        // contiguous bytes per column station), the
+                        // accumulator is released, and the same thread then
+                        // converts and stores them to global memory while
+                        // the MMAs of the next tile run. Each thread reads
+                        // back only what it wrote, so no barrier or fence is
+                        // needed, and a slot is rewritten only by its own
+                        // thread after it has been read back.
+                        auto stage = [&](int k, const uint32_t(&vr)[16], const uint32_t(&vi)[16]) {
+                            const uint32_t slot = stg_base + (uint32_t)k * STG_GROUP_BYTES + lane * 16u;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                sts128(slot + j * 512, make_uint4(vr[2 * j], vi[2 * j], vr[2 * j + 1], vi[2 * j + 1]));
+                        };
+                        auto release = [&]() {  // every column of this chunk has been read
+                            tc_fence_before();
+                            mbar_arrive(&bars->acc_empty[buf]);
+                            released = true;
+                        };
+                        tmem_ld_32x32b_x16(taddr + ndirect * 16, ra);
+                        tmem_ld_32x32b_x16(taddr + IMOFF + ndirect * 16, ia);
+                        tmem_wait_ld();
+                        if (nst == 1) release();
+#pragma unroll 1
+                        for (int k = 0; k < nst; k += 2) {
+                            const bool has1 = k + 1 < nst;
+                            const bool has2 = k + 2 < nst;
+                            if (has1) {
+                                tmem_ld_32x32b_x16(taddr + (ndirect + k + 1) * 16, rb2);
+                                tmem_ld_32x32b_x16(taddr + IMOFF + (ndirect + k + 1) * 16, ib2);
+                            }
+                            stage(k, ra, ia);
+                            if (has1) {
+                                tmem_wait_ld();
+                                if (k + 1 == nst - 1) release();
+                                if (has2) {
+                                    tmem_ld_32x32b_x16(taddr + (ndirect + k + 2) * 16, ra);
+                                    tmem_ld_32x32b_x16(taddr + IMOFF + (ndirect + k + 2) * 16, ia);
+                                }
+                                stage(k + 1, rb2, ib2);
+                                if (has2) {
+                                    tmem_wait_ld();
+                                    if (k + 2 == nst - 1) release();
+                                }
+                            }
+                        }
+                        // drain: the staged groups to global memory
+#pragma unroll 1
+                        for (int k = 0; k < nst; ++k) {
+                            const uint32_t slot = stg_base + (uint32_t)k * STG_GROUP_BYTES + lane * 16u;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const uint4 v = lds128(slot + j * 512);
+                                ra[2 * j] = v.x;
+                                ia[2 * j] = v.y;
+                                ra[2 * j + 1] = v.z;
+                                ia[2 * j + 1] = v.w;
+                            }
+                            store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + (ndirect + k) * 8, false,
+                                                  true, ra, ia);
+                        }
                     }
                 }
                 if (!released) {
@@ -985,11 +1094,14 @@ template <int DT, int V, int NPOL> const void *kernel_ptr()
         return reinterpret_cast<const void *>(&tc_correlate_kernel<DT, V, NPOL>);
 }
 
-template <int DT, int V> size_t smem_total() { return (size_t)smem_bytes<DT, V>() + sizeof(Bars) + 1024; }
+template <int DT, int V, int NPOL> size_t smem_total()
+{
+    return (size_t)smem_bytes<DT, V, NPOL>() + sizeof(Bars) + 1024;
+}
 
 template <int DT, int V, int NPOL> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
 {
-    const size_t smem = smem_total<DT, V>();
+    const size_t smem = smem_total<DT, V, NPOL>();
     cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V, NPOL>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1009,7 +1121,7 @@ template <int DT, int NPOL> cudaError_t launch_dt(int variant, const TcParams &p
 
 template <int DT> cudaError_t pair_clusters_dt(int *n)
 {
-    const size_t smem = smem_total<DT, TC_PAIR>();
+    const size_t smem = smem_total<DT, TC_PAIR, 2>();
     cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT, 2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
