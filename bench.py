@@ -14,6 +14,13 @@ Correlator ops = 32 per baseline per sample (8 per complex multiply-add,
 4 polarisation pairs), baselines S(S+1)/2 (Section 2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--split none|channels]
+
+Under torchrun each rank correlates on its own GPU with no collective on the
+data path. --split none (default): every rank runs the whole workload (weak
+scaling); --split channels: the workload's channels are divided over the
+ranks (strong scaling, the partition of Sections 2 and 7). Either way the
+line reports the ops of all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -40,7 +47,7 @@ TC_SOURCES = [os.path.join(ROOT, "paper_1702_00844_gb300", "csrc", f)
               for f in ("corr_tc.cu", "ptx.cuh", "corr_tc_internal.h")]
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -54,11 +61,35 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/FP32/batch/adjoint side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    return ap.parse_args()
+    ap.add_argument("--split", choices=["none", "channels"], default="none",
+                    help="none: every rank runs the whole workload (weak scaling); channels: the "
+                         "workload's channels are divided over the ranks (strong scaling)")
+    return ap.parse_args(argv)
 
 
 def ops_of(S, T, units):
     return 32.0 * S * (S + 1) / 2 * T * units
+
+
+# ------------------------------------------------------------- rank logic
+def rank_channels(split: str, n_channels: int, world: int, rank: int):
+    """[lo, hi) of the workload's channels this rank correlates: all of them
+    for split "none" (weak scaling), a contiguous share for "channels"
+    (strong scaling; the first n_channels % world ranks take one more)."""
+    from paper_1702_00844_gb300.shard import channel_range
+    if split == "channels":
+        return channel_range(n_channels, world, rank)
+    return 0, n_channels
+
+
+def job_throughput(ops_rank: float, ms_rank: float, steps: int, device=None):
+    """Job-wide correlator TOPS and ms per step: the ops of all ranks over
+    the slowest rank's time for `steps` steps (ms_rank is that rank's total
+    over the steps). Returns (TOPS, ms per step, total ops per step)."""
+    from paper_1702_00844_gb300.shard import max_over_ranks, sum_over_ranks
+    ops = sum_over_ranks(ops_rank, device=device)
+    ms = max_over_ranks(ms_rank, device=device)
+    return ops * steps / (ms * 1e-3) / 1e12, ms / steps, ops
 
 
 # ------------------------------------------------------------------ clocks
@@ -349,9 +380,15 @@ def run_ours(args):
     dev = torch.cuda.current_device()
 
     wl = args.workload
-    x8 = synth.precision_device(C3, S3, T3, "cuda", rank=rank)
+    # this rank's channels of the workload (all of them unless --split channels)
+    c_lo, c_hi = rank_channels(args.split, 256 if wl == "production" else C3, world, rank)
+    # weak scaling: a workload of its own per rank; strong: this rank's
+    # share of the one workload
+    split = args.split == "channels"
+    x8 = synth.precision_device(c_hi - c_lo if wl != "production" else C3, S3, T3, "cuda",
+                                rank=0 if split else rank, first_channel=c_lo if split else 0)
     if wl == "production":
-        S, C, T, I = 64, 256, 768, 10
+        S, C, T, I = 64, c_hi - c_lo, 768, 10
         gen = torch.Generator(device="cuda")
         gen.manual_seed(synth.BASE_SEED + 2 + 7919 * rank)
         x = torch.randn((I, C, S, T, 2), dtype=torch.complex64, device="cuda", generator=gen)
@@ -360,7 +397,7 @@ def run_ours(args):
         workload = ("production: 64 stations, 2 pols, 256 channels, 768 samples, 10 integrations, "
                     "complex64 N(0,1), FP32 CUDA-core path")
     else:
-        S, C, T, I = S3, C3, T3, 1
+        S, C, T, I = S3, c_hi - c_lo, T3, 1
         if wl == "precision-f16":
             x = x8.to(torch.float16)
             plan = Plan(S, C, T, dtype="cf16", path="tensor")
@@ -394,24 +431,31 @@ def run_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         time.sleep(0.3)
+        # the timed steps: nothing between the launches (an event between the
+        # int8 path's checked launch and its redo launch would keep the redo
+        # launch from being scheduled ahead as a programmatic dependent)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for a, b in kev:
-            plan.set_kernel_events(a, b)
+        for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        # the same steps again with a pair of events around each step's main
+        # kernel launch (corr_set_kernel_events): the roofline's per-launch
+        # duration of the dominant kernel
+        for a, b in kev:
+            plan.set_kernel_events(a, b)
+            step()
+        torch.cuda.synchronize()
     plan.set_kernel_events()
     kernel_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in kev) / len(kev), device="cuda")
-    ms_total = max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    ops = ops_of(S, T, units)
+    value, ms_step, ops_job = job_throughput(ops, e0.elapsed_time(e1), args.steps, device="cuda")
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     plan.check_error()
-    ms_step = ms_total / args.steps
-    ops = ops_of(S, T, units)
-    value = ops * world * args.steps / (ms_total * 1e-3) / 1e12
 
     # end to end through the public API with host buffers: corr_correlate_host
     # streams the step's samples from page-locked memory in chunks, with the
@@ -424,8 +468,8 @@ def run_ours(args):
     e2e_steps = max(1, min(args.steps, 5))
     e2e_ms = time_launches(lambda: plan_io.correlate_host(xh, oh), e2e_steps, 1, stream)
     plan_io.check_error()
-    e2e_ms = max_over_ranks(e2e_ms, device="cuda")
-    e2e = {"value": ops * world / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+    e2e_val, e2e_ms, _ = job_throughput(ops, e2e_ms, 1, device="cuda")
+    e2e = {"value": e2e_val, "unit": UNIT,
            "h2d_bytes_per_step": xh.numel() * xh.element_size(),
            "d2h_bytes_per_step": oh.numel() * oh.element_size(), "ms_per_step": e2e_ms,
            "api": "corr_correlate_host (chunked, copies overlapped with kernels)"}
@@ -435,16 +479,17 @@ def run_ours(args):
     in_bps = {"s8": 4, "f16": 8, "f32": 16}[dtype_label]
     alg_bytes = units * (S * T * in_bps + S * (S + 1) // 2 * 32)
     # the dominant kernel's own launches (events around the main launch of
-    # each step), as the roofline asks; ms_per_step also holds the int8 redo
-    # launch and its two small memsets
+    # each step), as the roofline asks; ms_per_step also holds the int8 path's
+    # redo launch (empty on this data)
     achieved = ops / (kernel_ms * 1e-3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if wl == "production":
-        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x maximum SM clock
-        peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        # FP32 FMA pipe: this device's SMs x 128 FP32 lanes x 2 flops x maximum SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "fp32_correlate_kernel",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"}
+                "peak_source": f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flops x max SM clock"}
     else:
         peak = float(peaks.get("bf16_tflops", 1900.0))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -455,13 +500,15 @@ def run_ours(args):
                 "peak_source": f"{peak_src} bf16 dense burst (f16 dense runs at the bf16 rate)"}
     roof["algorithmic_bytes"] = alg_bytes
     roof["kernel_ms"] = kernel_ms
-    roof["timing"] = ("CUDA events around the main kernel launch of each timed step "
+    roof["timing"] = ("CUDA events around the main kernel launch of each step of a second pass "
+                      "over the timed steps inside the clock-sampled region "
                       "(corr_set_kernel_events), averaged")
     roof["hbm_bound_TOPS"] = ops / (alg_bytes / (hbm * 1e9)) / 1e12
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.split == "channels" else "weak",
+            "vs_baseline": None,
             "dtype": dtype_label,
             "data": "synthetic (seeded device Philox, same recipe as the workload)",
             "config": {"workload": workload, "stations": S, "pols": 2, "channels": C,
@@ -474,7 +521,10 @@ def run_ours(args):
                        "l2": f"inputs {units * S * T * in_bps / 1e6:.0f} MB and outputs "
                              f"{units * S * (S + 1) // 2 * 32 / 1e6:.0f} MB; inputs exceed L2 "
                              "(129 MB): no flush",
-                       "parallelism": f"channels per GPU fixed, {world} GPU(s), no collective"},
+                       "parallelism": (f"{world} GPU(s), the workload's channels split over them "
+                                       f"(this rank: {c_hi - c_lo} of {c_hi - c_lo if args.split == 'none' else (256 if wl == 'production' else C3)}), no collective"
+                                       if args.split == "channels" else
+                                       f"channels per GPU fixed, {world} GPU(s), no collective")},
             "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
             # one tensor launch per step, plus the (usually empty) redo launch
             # of the int8 path when T exceeds one 512-sample chunk

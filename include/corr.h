@@ -150,7 +150,9 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
  * over channels, baselines and pol pairs. d_raw_vis, d_vis_model: complex
  * float32 [units][B][2][2]; d_gain: complex float32 [units][S][2];
  * d_vis_out (nullable) receives V; d_loss (nullable) receives L (float32).
- * Requires a plan created with CORR_FLAG_GAINS and dtype CORR_CF32. */
+ * Complex buffers must be 8-byte aligned, d_loss 4-byte aligned
+ * (CORR_ERR_INVALID_ARG otherwise). Requires a plan created with
+ * CORR_FLAG_GAINS and dtype CORR_CF32. */
 corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void *d_gain,
                              const void *d_vis_model, void *d_vis_out, float *d_loss,
                              void *stream);
@@ -163,8 +165,11 @@ corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void 
  *   d_grad_in (nullable): same layout as d_in (complex float32),
  *       dL/d conj(x_c(t)) = conj(g_c) sum_b W_cb g_b x_b(t),
  *       W_cb = [s_c<=s_b] E_cb + [s_b<=s_c] conj(E_bc), E = V - M;
- *   d_raw_vis (nullable): R from a previous corr_correlate; recomputed if NULL;
- *   d_loss (nullable): receives L. */
+ *   d_raw_vis (nullable): R from a previous corr_correlate; recomputed if NULL
+ *       (d_in must then be 16-byte aligned, as for corr_correlate);
+ *   d_loss (nullable): receives L.
+ * Complex buffers must be 8-byte aligned, d_loss and d_grad_scale 4-byte
+ * aligned (CORR_ERR_INVALID_ARG otherwise). */
 corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *d_gain,
                                  const void *d_vis_model, const void *d_raw_vis,
                                  void *d_grad_gain, void *d_grad_in, float *d_loss,
@@ -249,9 +254,13 @@ const char *corr_last_error_message(void);
  * library holds on every GPU that loads it, until the process exits. Larger
  * problems are rejected with CORR_ERR_UNSUPPORTED and a message in
  * corr_last_error_message. Nothing in the array needs to start at zero;
- * every call overwrites what it uses. The first call on a device looks up
- * the array's device address with that device current (a synchronous
- * runtime call), so make it before any stream capture. All calls share the
+ * every call overwrites what it uses. The first call in a device's context
+ * looks up the array's device address with that device current (a
+ * synchronous runtime call), so make it before any stream capture; the
+ * address is cached with the context's ID and looked up again in a new
+ * context of the device (after cudaDeviceReset, for example). Complex
+ * buffers must be 8-byte aligned, d_loss and d_grad_scale 4-byte aligned
+ * (CORR_ERR_INVALID_ARG otherwise). All calls share the
  * one array: calls whose kernels overlap on the GPU (different streams
  * without ordering) race and give wrong results. No cudaMalloc, cudaFree or
  * allocating library routine is called. Asynchronous on stream. */

@@ -38,8 +38,10 @@ struct corr_plan {
     int tc_variant = TC_NARROW;
     int pair_clusters = 0;     // clusters of the pair variant resident at once (0: unavailable)
     float tune_ms[TC_N_VARIANTS] = {0.f, 0.f, 0.f};
-    // int8 power check / redo list (single problem and batches)
-    int *d_redo_mark = nullptr;
+    // int8 power check / redo list (single problem and batches): state =
+    // {count, done} of the main and the tail list, then one mark per item
+    int *d_redo_state = nullptr;
+    int *d_redo_index = nullptr;
     int4 *d_redo_items = nullptr;
     int redo_cap = 0;
     // ragged batches
@@ -70,6 +72,8 @@ thread_local char g_last_error[256] = "";
 constexpr int TC_SIDE = TC_RS;
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// Alignment the gain kernels need: complex float32 values (8 bytes), floats (4).
+bool aligned_to(const void *p, uintptr_t a) { return !p || (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 long long n_baselines(long long S) { return S * (S + 1) / 2; }
 
@@ -257,17 +261,23 @@ corr_status_t cuda_status(cudaError_t e)
 corr_status_t ensure_redo(corr_plan *h, int n)
 {
     if (n <= h->redo_cap) return CORR_OK;
-    cudaFree(h->d_redo_mark);
+    cudaFree(h->d_redo_state);
+    cudaFree(h->d_redo_index);
     cudaFree(h->d_redo_items);
-    h->d_redo_mark = nullptr;
+    h->d_redo_state = nullptr;
+    h->d_redo_index = nullptr;
     h->d_redo_items = nullptr;
     h->redo_cap = 0;
     corr_status_t st;
-    // per item list (ctr 0 and 1) its counter directly followed by its marks,
-    // so that one memset clears both: list (redo_off, ctr) uses entries
-    // redo_off + ctr (counter) and redo_off + ctr + 1 ... (marks)
-    if ((st = cuda_status(cudaMalloc(&h->d_redo_mark, ((size_t)n + 2) * sizeof(int)))) != CORR_OK) return st;
+    // {count, done} of the main list (ctr 0) and the tail list (ctr 1), then
+    // the marks; list (redo_off, ctr) uses marks, indices and items from
+    // redo_off on. Zeroed once here; each redo launch leaves it zeroed again.
+    const size_t state_bytes = ((size_t)n + 4) * sizeof(int);
+    if ((st = cuda_status(cudaMalloc(&h->d_redo_state, state_bytes))) != CORR_OK) return st;
+    if ((st = cuda_status(cudaMalloc(&h->d_redo_index, (size_t)n * sizeof(int)))) != CORR_OK) return st;
     if ((st = cuda_status(cudaMalloc(&h->d_redo_items, (size_t)n * sizeof(int4)))) != CORR_OK) return st;
+    if ((st = cuda_status(cudaMemset(h->d_redo_state, 0, state_bytes))) != CORR_OK) return st;
+    if ((st = cuda_status(cudaDeviceSynchronize())) != CORR_OK) return st;
     h->redo_cap = n;
     return CORR_OK;
 }
@@ -305,26 +315,33 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
         if (mark) cudaEventRecord(h->ev_k1, s);
         return st;
     }
-    int *count = h->d_redo_mark + redo_off + ctr;
-    corr_status_t st = cuda_status(cudaMemsetAsync(count, 0, ((size_t)p.n_items + 1) * sizeof(int), s));
-    if (st != CORR_OK) return st;
+    // The list is empty when a call starts: the previous redo launch left it
+    // so (no memset per call).
+    int *count = h->d_redo_state + 2 * ctr;
     TcParams a = p;
     a.chunk_kb = 0;
     a.check_power = 1;
-    a.redo_mark = count + 1;
+    a.redo_mark = h->d_redo_state + 4 + redo_off;
     a.redo_items = h->d_redo_items + redo_off;
+    a.redo_index = h->d_redo_index + redo_off;
     a.redo_count = count;
+    a.redo_done = nullptr;
     if (mark) cudaEventRecord(h->ev_k0, s);
-    st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
+    corr_status_t st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
     if (mark) cudaEventRecord(h->ev_k1, s);
     if (st != CORR_OK) return st;
-    TcParams b = p;
+    // the chunked redo launch over the rejected items (usually none), as a
+    // programmatic dependent: its CTAs are scheduled while the checked launch
+    // ends and wait for it before reading the count, so an empty list costs
+    // no launch gap
+    TcParams b = a;
     b.items = h->d_redo_items + redo_off;
     b.n_items = p.n_items;          // upper bound; the count is read on the device
     b.n_items_dev = count;
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
-    return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s));
+    b.redo_done = count + 1;
+    return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s, true));
 }
 
 // The main list of p in `variant`, then (pair variant) the n_tail narrow
@@ -920,6 +937,9 @@ corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void 
 {
     if (!h || !d_raw_vis || !d_gain || !d_vis_model) return CORR_ERR_INVALID_ARG;
     if (!(h->d.flags & CORR_FLAG_GAINS)) return CORR_ERR_INVALID_ARG;
+    if (!aligned_to(d_raw_vis, 8) || !aligned_to(d_gain, 8) || !aligned_to(d_vis_model, 8) ||
+        !aligned_to(d_vis_out, 8) || !aligned_to(d_loss, 4))
+        return CORR_ERR_INVALID_ARG;
     const int units = h->d.n_channels * h->d.n_integrations;
     return cuda_status(gain_loss_launch(static_cast<const float2 *>(d_raw_vis),
                                         static_cast<const float2 *>(d_gain),
@@ -936,6 +956,10 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     if (!h || !d_gain || !d_vis_model || !d_grad_gain) return CORR_ERR_INVALID_ARG;
     if (!(h->d.flags & CORR_FLAG_GAINS)) return CORR_ERR_INVALID_ARG;
     if ((!d_raw_vis || d_grad_in) && !d_in) return CORR_ERR_INVALID_ARG;
+    if (!aligned_to(d_in, 8) || !aligned_to(d_gain, 8) || !aligned_to(d_vis_model, 8) ||
+        !aligned_to(d_raw_vis, 8) || !aligned_to(d_grad_gain, 8) || !aligned_to(d_grad_in, 8) ||
+        !aligned_to(d_loss, 4) || !aligned_to(d_grad_scale, 4))
+        return CORR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int units = h->d.n_channels * h->d.n_integrations;
     const int S = h->d.n_stations;
@@ -1027,7 +1051,8 @@ corr_status_t corr_destroy(corr_handle_t h)
     cudaFree(h->d_err);
     cudaFree(h->d_fp_partial);
     cudaFree(h->d_items);
-    cudaFree(h->d_redo_mark);
+    cudaFree(h->d_redo_state);
+    cudaFree(h->d_redo_index);
     cudaFree(h->d_redo_items);
     cudaFree(h->d_bprobs);
     cudaFree(h->d_bitems);

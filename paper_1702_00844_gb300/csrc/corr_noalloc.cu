@@ -10,9 +10,13 @@
 //
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds it until the process exits. Host code cannot use the array's
-// name as a device address: on first use on a device, with that device
-// current, the address is looked up once with cudaGetSymbolAddress and
-// cached.
+// name as a device address: on the first call in a device's context, with
+// that device current, the address is looked up with cudaGetSymbolAddress
+// and cached together with the context's ID. A later call in another context
+// of the device (after cudaDeviceReset, or after the primary context was
+// released and created again, when the module is loaded anew and the array
+// may move) looks the address up again instead of using a stale one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -30,6 +34,39 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context ID the address belongs to
+
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+
+// ID of the calling thread's current context (driver entry points, resolved
+// once); 0 if it cannot be read, in which case the address is looked up on
+// every call.
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+                cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+                cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrent>(a);
+            get_id = reinterpret_cast<CtxGetId>(b);
+        }
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 corr_status_t scratch_on_current_device(void **out)
 {
@@ -40,8 +77,9 @@ corr_status_t scratch_on_current_device(void **out)
         return CORR_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) return CORR_ERR_UNSUPPORTED;
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -49,12 +87,15 @@ corr_status_t scratch_on_current_device(void **out)
             return CORR_ERR_CUDA;
         }
         g_scratch_addr[dev] = p;
+        // the lookup made the device's context current if it was not
+        g_scratch_ctx[dev] = current_ctx_id();
     }
     *out = g_scratch_addr[dev];
     return CORR_OK;
 }
 
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// The kernels read and write complex values (8 bytes) and floats (4 bytes).
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 } // namespace
 
@@ -70,9 +111,11 @@ extern "C" corr_status_t corr_gain_backward_noalloc(int n_stations, int n_units,
     if (n_stations < 1 || n_units < 1 || n_samples < 0) return CORR_ERR_INVALID_ARG;
     if (!d_gain || !d_vis_model || !d_raw_vis || !d_grad_gain) return CORR_ERR_INVALID_ARG;
     if (d_grad_in && n_samples > 0 && !d_in) return CORR_ERR_INVALID_ARG;
-    const void *ptrs[] = {d_in, d_gain, d_vis_model, d_raw_vis, d_grad_gain, d_grad_in, d_loss};
-    for (const void *q : ptrs)
-        if (q && !aligned16(q)) return CORR_ERR_INVALID_ARG;
+    const void *cplx[] = {d_in, d_gain, d_vis_model, d_raw_vis, d_grad_gain, d_grad_in};
+    for (const void *q : cplx)
+        if (q && !aligned(q, 8)) return CORR_ERR_INVALID_ARG;
+    if ((d_loss && !aligned(d_loss, 4)) || (d_grad_scale && !aligned(d_grad_scale, 4)))
+        return CORR_ERR_INVALID_ARG;
 
     // scratch layout: loss partials (one float per channel), then W'
     const size_t n = 2 * (size_t)n_stations;

@@ -444,6 +444,23 @@ __device__ __forceinline__ Item get_item(const TcParams &p, int i)
     return Item{v.x, v.y, v.z, v.w & 0xFFFF, v.w >> 16};
 }
 
+// Redo launch: counts this CTA as finished; the last CTA of the grid (every
+// CTA has read the redo count by then) clears the marks of the listed items
+// and zeroes the count and itself, ready for the next call.
+__device__ __forceinline__ void redo_finish(const TcParams &p)
+{
+    if (!p.redo_done || threadIdx.x != 0) return;
+    __threadfence();
+    if (atomicAdd(p.redo_done, 1) != (int)gridDim.x - 1) return;
+    __threadfence();
+    volatile int *count = p.redo_count;
+    const int n = *count;
+    for (int i = 0; i < n; ++i) p.redo_mark[p.redo_index[i]] = 0;
+    *count = 0;
+    *reinterpret_cast<volatile int *>(p.redo_done) = 0;
+    __threadfence();
+}
+
 __device__ __forceinline__ TcProblem get_prob(const TcParams &p, int k)
 {
     return p.probs ? p.probs[k] : p.prob0;
@@ -580,6 +597,10 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
+    // The redo launch reads the count that the launch before it wrote: wait
+    // for that launch's end. Any launch lets its own dependent be scheduled.
+    if (p.n_items_dev) griddep_wait();
+    griddep_launch_dependents();
     const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
     // A pair (cluster of 2 CTAs) shares each work item; rank 0 issues the MMAs.
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
@@ -588,7 +609,10 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
     const int item_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     // No work (e.g. an empty redo list): leave before any barrier, TMEM or
     // cluster step. Both CTAs of a pair see the same item0 and leave together.
-    if (item0 >= n_items) return;
+    if (item0 >= n_items) {
+        redo_finish(p);
+        return;
+    }
 
     // In a pair, the even CTA's full and acc_empty barriers also count one
     // arrival of the odd CTA's relay thread (see the relay below).
@@ -769,6 +793,7 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
                     if (atomicExch(p.redo_mark + it, 1) == 0) {
                         const int slot = atomicAdd(p.redo_count, 1);
                         p.redo_items[slot] = __ldg(p.items + it);
+                        p.redo_index[slot] = it;
                     }
                 }
             }
@@ -1071,6 +1096,7 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
         else
             tmem_dealloc(tmem_base, TMEM_COLS);
     }
+    redo_finish(p);
 }
 
 template <int DT, int V, int NPOL>
@@ -1099,12 +1125,29 @@ template <int DT, int V, int NPOL> size_t smem_total()
     return (size_t)smem_bytes<DT, V, NPOL>() + sizeof(Bars) + 1024;
 }
 
-template <int DT, int V, int NPOL> cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s)
+template <int DT, int V, int NPOL>
+cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, bool pdl)
 {
     const size_t smem = smem_total<DT, V, NPOL>();
     cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V, NPOL>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid, 1, 1);
+        cfg.blockDim = dim3(TC_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if constexpr (V == TC_PAIR)
+            return cudaLaunchKernelEx(&cfg, tc_pair_kernel<DT, NPOL>, p);
+        else
+            return cudaLaunchKernelEx(&cfg, tc_correlate_kernel<DT, V, NPOL>, p);
+    }
     if constexpr (V == TC_PAIR)
         tc_pair_kernel<DT, NPOL><<<grid, TC_THREADS, smem, s>>>(p);
     else
@@ -1112,11 +1155,12 @@ template <int DT, int V, int NPOL> cudaError_t launch_one(const TcParams &p, int
     return cudaGetLastError();
 }
 
-template <int DT, int NPOL> cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s)
+template <int DT, int NPOL>
+cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s, bool pdl)
 {
-    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR, NPOL>(p, grid, s);
-    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE, NPOL>(p, grid, s);
-    return launch_one<DT, TC_NARROW, NPOL>(p, grid, s);
+    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR, NPOL>(p, grid, s, pdl);
+    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE, NPOL>(p, grid, s, pdl);
+    return launch_one<DT, TC_NARROW, NPOL>(p, grid, s, pdl);
 }
 
 template <int DT> cudaError_t pair_clusters_dt(int *n)
@@ -1134,12 +1178,12 @@ template <int DT> cudaError_t pair_clusters_dt(int *n)
 
 } // namespace
 
-cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s)
+cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s, bool pdl)
 {
     if (variant == TC_PAIR && (grid < 2 || grid % 2 != 0)) return cudaErrorInvalidValue;
     if (npol == 1)
-        return dtype == 1 ? launch_dt<1, 1>(variant, p, grid, s) : launch_dt<2, 1>(variant, p, grid, s);
-    return dtype == 1 ? launch_dt<1, 2>(variant, p, grid, s) : launch_dt<2, 2>(variant, p, grid, s);
+        return dtype == 1 ? launch_dt<1, 1>(variant, p, grid, s, pdl) : launch_dt<2, 1>(variant, p, grid, s, pdl);
+    return dtype == 1 ? launch_dt<1, 2>(variant, p, grid, s, pdl) : launch_dt<2, 2>(variant, p, grid, s, pdl);
 }
 
 cudaError_t tc_pair_max_clusters(int dtype, int *n)

@@ -29,10 +29,15 @@ struct TcParams {
     // largest station power sum_t |x|^2 of its stations (Cauchy-Schwarz); a
     // tile whose bound exceeds 2^24 is appended once to the redo list, which
     // a second, chunked launch recomputes (overwriting its output).
+    // The list cleans up after itself: the redo launch's last CTA clears the
+    // marks of the items it held and zeroes the count, so no call needs a
+    // memset first.
     int check_power;
-    int *redo_mark;           // per item: 0, or 1 once appended (zeroed per call)
+    int *redo_mark;           // per item: 0, or 1 once appended
     int4 *redo_items;
+    int *redo_index;          // item index of each appended entry
     int *redo_count;
+    int *redo_done;           // redo launch only: CTAs finished (the last one resets the list)
     int *err;                 // device error word
     unsigned long long wait_ns;
 };
@@ -51,7 +56,11 @@ constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 
 // grid: CTAs (even for TC_PAIR: two per cluster). npol: 1 or 2 polarisations
 // (with 1, the items are over pseudo-stations of two stations each).
-cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s);
+// pdl: launched as a programmatic dependent of the previous kernel on the
+// stream (the redo launch; the kernel waits for that kernel's completion
+// before it reads the redo count).
+cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s,
+                      bool pdl = false);
 // Clusters of the pair variant that fit on the device at once.
 cudaError_t tc_pair_max_clusters(int dtype, int *n);
 

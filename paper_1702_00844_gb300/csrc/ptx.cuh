@@ -119,6 +119,19 @@ static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t
     }
 }
 
+// ------------------------------------------------- programmatic dependent launch
+// Waits until the kernel this one depends on (launched before it on the
+// stream) has completed and its memory operations are visible; returns at
+// once if the kernel was not launched as a programmatic dependent.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Lets a kernel launched as this kernel's programmatic dependent be
+// scheduled (its CTAs still wait in griddep_wait for this kernel's end).
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ clusters
 __device__ __forceinline__ uint32_t cluster_ctarank()
 {

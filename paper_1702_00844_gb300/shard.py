@@ -35,6 +35,19 @@ def max_over_ranks(value: float, group=None, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, group=None, device=None) -> float:
+    """Sum of ``value`` over the ranks of ``group`` (identity without an
+    initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item())
+
+
 def corner_turn(x_local, S: int, C: int, T: int, I: int, dtype: str, group=None, reorder_fn=None):
     """The FX corner turn of Section 7 over the ranks of ``group``: before the
     exchange every rank holds all channels of its own stations, afterwards

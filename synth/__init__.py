@@ -188,17 +188,20 @@ def differentiation(C: int = 64, S: int = 64, T: int = 1024, seed_offset: int = 
 
 
 def precision_device(C: int = 480, S: int = 256, T: int = 1024, device="cuda",
-                     seed_offset: int = 3, rank: int = 0):
+                     seed_offset: int = 3, rank: int = 0, first_channel: int = 0):
     """Workload 3 drawn on the device (torch Philox stream): complex int8 from
     N(0, 32^2), rounded and clipped to +-127, shape ``(C, S, T, P, 2)``.
-    Same recipe as ``precision`` (different stream), for full-size runs."""
+    Same recipe as ``precision`` (different stream), for full-size runs.
+    Each channel has its own seed, so channels ``first_channel ..
+    first_channel + C - 1`` are the same values whoever draws them (a rank's
+    share of a workload split over ranks); ``rank`` gives a rank a workload
+    of its own instead."""
     import torch
     gen = torch.Generator(device=device)
-    gen.manual_seed((BASE_SEED + seed_offset) * 7919 + rank)
+    base = ((BASE_SEED + seed_offset) * 7919 + rank) * 65536
     out = torch.empty((C, S, T, P, 2), dtype=torch.int8, device=device)
-    step = max(1, C // 8)
-    for c0 in range(0, C, step):
-        c1 = min(C, c0 + step)
-        v = torch.randn((c1 - c0, S, T, P, 2), generator=gen, device=device) * 32.0
-        out[c0:c1] = v.round_().clamp_(-127, 127).to(torch.int8)
+    for c in range(C):
+        gen.manual_seed(base + first_channel + c)
+        v = torch.randn((S, T, P, 2), generator=gen, device=device) * 32.0
+        out[c] = v.round_().clamp_(-127, 127).to(torch.int8)
     return out

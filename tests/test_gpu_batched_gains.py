@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import TOL_FP16, rel_frobenius_per_unit, to_numpy_int, to_numpy_vis, tol_fp16
+from helpers import TOL_FP16, coef_error, rel_frobenius_per_unit, to_numpy_int, to_numpy_vis, tol_fp16
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,6 +46,9 @@ def check_batch(dtype, outs, hosts):
             got = to_numpy_vis(o, "cf16")
             assert np.isfinite(got).all()
             assert rel_frobenius_per_unit(got, ref).max() < TOL_FP16
+            # element-wise too: one wrong baseline cannot hide under the norm
+            if T:
+                assert coef_error(got, ref, S) < 1e-4
 
 
 @pytest.mark.parametrize("variant", ["narrow", "wide", "pair"])
@@ -252,7 +255,8 @@ def test_batching_workload_full_size_sampled():
     samples) in the benchmark's launch configuration: one persistent launch,
     captured in a CUDA graph and replayed, with the tile variant the batch
     heuristic picks. One sampled channel of every sub-array is compared with
-    the oracle on the same f16 values (relative Frobenius norm), and every
+    the oracle on the same f16 values (relative Frobenius norm and, element
+    by element, the correlation-coefficient error), and every
     channel's XX/YY autocorrelations are checked positive with an imaginary
     part at FP32 rounding level (the +a_i a_r and -a_r a_i terms are summed
     in different MMA steps)."""
@@ -283,6 +287,7 @@ def test_batching_workload_full_size_sampled():
         got = o[c:c + 1].cpu().numpy().astype(np.complex128)
         assert np.isfinite(got).all(), k
         assert rel_frobenius_per_unit(got, ref).max() < tol_fp16(T), k
+        assert coef_error(got, ref, S) < 1e-4, k
         auto = o[:, [s * (s + 1) // 2 + s for s in range(S)]]        # (C, S, 2, 2)
         xx_yy = torch.stack([auto[..., 0, 0], auto[..., 1, 1]], -1)
         assert bool((xx_yy.real > 0).all()), k

@@ -1,10 +1,16 @@
 """corr_correlate_host: host buffers streamed in chunks with the copies
 overlapping the kernels must give exactly what corr_correlate gives on
-device buffers (both kernel paths, several chunks and a ragged last chunk)."""
+device buffers (both kernel paths, several chunks and a ragged last chunk),
+and match the FP64 oracle on sampled channels (the first, one in the middle
+and the last, so that the first, a middle and the ragged last chunk are
+covered): bit for bit for int8, within the accumulation tolerances for f16
+and FP32 samples."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from helpers import TOL_FP32, coef_error, rel_frobenius_per_unit, to_numpy_int, to_numpy_vis, tol_fp16
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,6 +38,18 @@ def test_host_streaming_equals_device_call(dtype, S, C, T):
     assert torch.equal(oh, ref)
     if T:
         assert bool((oh != 0).any())
+    xs = x.numpy()
+    for c in sorted({0, C // 2, C - 1}):
+        want = oracle.correlate(xs[c][None], dtype)
+        if dtype == "ci8":
+            got = to_numpy_int(oh[0, c][None])
+            np.testing.assert_array_equal(got[..., 0], want.real.astype(np.int64))
+            np.testing.assert_array_equal(got[..., 1], want.imag.astype(np.int64))
+        elif T:
+            got = to_numpy_vis(oh[0, c][None], dtype)
+            tol = tol_fp16(T) if dtype == "cf16" else TOL_FP32
+            assert rel_frobenius_per_unit(got, want).max() < tol
+            assert coef_error(got, want, S) < 1e-4
 
 
 def test_host_streaming_requires_the_flag():

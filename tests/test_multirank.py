@@ -76,6 +76,59 @@ def test_two_ranks_gloo(tmp_path):
     assert job_throughput([3, 5], tmax) == pytest.approx(8 / 1.5)
 
 
+def _bench_worker(rank, world, port, out_dir):
+    import json
+
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = {}
+    for split in ("none", "channels"):
+        lo, hi = bench.rank_channels(split, 480, world, rank)
+        ops = bench.ops_of(256, 1024, hi - lo)
+        # rank 1 pretends to be slower: 12 ms against 10 ms for the 4 steps
+        value, ms_step, ops_job = bench.job_throughput(ops, 10.0 + 2.0 * rank, 4)
+        res[split] = {"lo": lo, "hi": hi, "value": value, "ms_step": ms_step, "ops_job": ops_job}
+    with open(os.path.join(out_dir, f"bench{rank}.json"), "w") as f:
+        json.dump(res, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_rank_logic_two_ranks_gloo(tmp_path):
+    """bench.py's rank logic on two gloo ranks: with --split channels the
+    ranks own 240 channels each and the job's ops are those of the one
+    480-channel workload; without a split every rank runs all 480 and the
+    job counts both. Either way the time is the slowest rank's."""
+    pytest.importorskip("torch")
+    import json
+
+    import torch.multiprocessing as mp
+
+    import bench
+    port = _free_port()
+    mp.start_processes(_bench_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    r = [json.load(open(tmp_path / f"bench{k}.json")) for k in range(2)]
+    full = bench.ops_of(256, 1024, 480)
+    assert (r[0]["channels"]["lo"], r[0]["channels"]["hi"]) == (0, 240)
+    assert (r[1]["channels"]["lo"], r[1]["channels"]["hi"]) == (240, 480)
+    assert (r[1]["none"]["lo"], r[1]["none"]["hi"]) == (0, 480)
+    for k in range(2):
+        assert r[k]["channels"]["ops_job"] == pytest.approx(full)
+        assert r[k]["none"]["ops_job"] == pytest.approx(2 * full)
+        for split in ("none", "channels"):
+            assert r[k][split]["ms_step"] == pytest.approx(3.0)      # 12 ms / 4 steps
+            want = r[k][split]["ops_job"] * 4 / 12e-3 / 1e12
+            assert r[k][split]["value"] == pytest.approx(want)
+    assert bench.parse(["--split", "channels"]).split == "channels"
+    assert bench.parse([]).split == "none"
+
+
 def _np_reorder(x, S, C, T, I, dtype, a, b):
     """Test stand-in for corr_reorder on CPU tensors (the oracle's permutation)."""
     import torch
