@@ -310,7 +310,9 @@ def secondary(x8, torch):
     opsb = sum(ops_of(S, T, C) for S, C, T in shapes)
     res["tensor_fp16_ragged_batch"] = {"ms": ms, "TOPS": opsb / ms / 1e9, "ops": opsb,
                                        "input_GB": sum(x.numel() * 2 for x in xs) / 1e9,
-                                       "variant": pb.batch_tile_variant()}
+                                       "variant": pb.batch_tile_variant(),
+                                       "tuned": [["/".join(map(str, c)), round(t, 3)]
+                                                 for c, t in pb.tune_results(batch=True)]}
     pb.check_error()
     del xs, outs, pairs, g, pb
     torch.cuda.empty_cache()
@@ -526,6 +528,9 @@ def run_ours(args):
                                        if args.split == "channels" else
                                        f"channels per GPU fixed, {world} GPU(s), no collective")},
             "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+            "tile_config": (dict(plan.tile_config(),
+                                 tuned=[["/".join(map(str, c)), round(t, 4)] for c, t in plan.tune_results()])
+                            if wl != "production" else None),
             # one tensor launch per step, plus the (usually empty) redo launch
             # of the int8 path when T exceeds one 512-sample chunk
             "gpu_launches": args.steps * (2 if dtype_label == "s8" and T > 512 else 1)}

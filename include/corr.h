@@ -227,6 +227,27 @@ corr_status_t corr_set_kernel_events(corr_handle_t h, void *ev_start, void *ev_s
  * that set of sub-arrays; -1 before any batch or for NULL. */
 int corr_batch_tile_variant(corr_handle_t h);
 
+/* The tensor-path plan's tile configuration (Section 2's tiling of the
+ * correlation triangle, chosen by corr_create's autotuner): *variant (0
+ * narrow, 1 wide, 2 pair), *tail (the tail list's variant for pair tiles
+ * with an odd block count: 0 narrow, 1 wide), *layout (0, or 1 for the
+ * int8 pair kernel of two pols with the six-stage operand ring instead of
+ * staged epilogue groups) and *source: 0 forced by CORR_TC_VARIANT /
+ * CORR_TC_TAIL / CORR_TC_LAYOUT, 1 the size rule (CORR_FLAG_NO_AUTOTUNE or
+ * no samples), 2 timed in this corr_create, 3 cached earlier in this
+ * process, 4 read from the tuning cache file (CORR_TUNE_CACHE, "off" for
+ * none; default $XDG_CACHE_HOME/corr_gb300/tune.txt or
+ * ~/.cache/corr_gb300/tune.txt; lines of other library builds are ignored).
+ * Any output may be NULL. CORR_ERR_INVALID_ARG for a FP32-path plan. */
+corr_status_t corr_tile_config(corr_handle_t h, int *variant, int *tail, int *layout, int *source);
+
+/* The candidates the autotuner timed (batch = 0: in corr_create; 1: for the
+ * current ragged batch) with their times: cfg[3i..3i+2] = {variant, tail,
+ * layout}, ms[i] = milliseconds per run (batch: the best of two rounds).
+ * Fills up to cap entries (cfg and ms may be NULL) and returns the count
+ * (0 when nothing was timed), -1 for a NULL handle. Host-only. */
+int corr_tune_results(corr_handle_t h, int batch, int cap, int *cfg, float *ms);
+
 /* Reads and clears the plan's device error word (synchronous copy):
  * CORR_OK or CORR_ERR_TIMEOUT. */
 corr_status_t corr_get_error(corr_handle_t h);
@@ -284,6 +305,20 @@ void corr_tile_cost(int w, int h, long *flops, long *bytes, long *regs);
  * row and column block (rb <= cb). Returns -1 for k out of range. */
 int corr_tc_tiles(int n_stations);
 int corr_tc_tile_decode(int n_stations, int k, int *rb, int *cb);
+
+/* The tensor path's work tiles for one channel of n_stations stations in
+ * tile variant `variant` (0 narrow, 1 wide, 2 pair), in launch order: for
+ * tile k, out[4k..4k+3] = {row block, first column block, column blocks,
+ * list} over 64-station blocks, list 0 for the main launch and 1 for the
+ * second launch. The second list exists for the pair variant with an odd
+ * block count, in variant tail_kind: 0 (narrow) = the last block column as
+ * narrow tiles, pair tiles over blocks 0 .. nb-2; 1 (wide) = block 0's row
+ * as wide tiles, pair tiles over blocks 1 .. nb-1. A tile's row blocks are
+ * {rb} (narrow, wide) or {rb, rb+1} (pair); its column blocks cb0 .. cb0 +
+ * count - 1. With out == NULL returns the tile count; otherwise fills out
+ * and returns the count, or -1 if it exceeds cap (tiles) or the arguments
+ * are invalid. */
+int corr_tc_schedule(int variant, int tail_kind, int n_stations, int cap, int *out);
 
 /* Number of 4x4-station register tiles of the FP32 path per channel
  * (upper triangle, diagonal included) and the decode of tile k into its

@@ -74,10 +74,17 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.corr_tile_variant.restype = ip
     L.corr_batch_tile_variant.argtypes = [vp]
     L.corr_batch_tile_variant.restype = ip
+    L.corr_tile_config.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                   ctypes.POINTER(ip)]
+    L.corr_tile_config.restype = ip
+    L.corr_tune_results.argtypes = [vp, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_float)]
+    L.corr_tune_results.restype = ip
     L.corr_set_kernel_events.argtypes = [vp, vp, vp]
     L.corr_set_kernel_events.restype = ip
     L.corr_tc_tiles.argtypes = [ip]
     L.corr_tc_tile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.corr_tc_schedule.argtypes = [ip, ip, ip, ip, ctypes.POINTER(ip)]
+    L.corr_tc_schedule.restype = ip
     L.corr_fp32_subtiles.argtypes = [ip]
     L.corr_fp32_subtile_decode.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.corr_gain_backward_noalloc.argtypes = [ip, ip, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -246,6 +253,27 @@ class Plan:
         a = start._as_parameter_ if start is not None else None
         b = stop._as_parameter_ if stop is not None else None
         _check(self.L.corr_set_kernel_events(self.h, a, b), "corr_set_kernel_events")
+
+    def tile_config(self) -> dict:
+        """``corr_tile_config``: the tensor-path tile configuration and how it
+        was chosen."""
+        v, t, l, src = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.L.corr_tile_config(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(l),
+                                       ctypes.byref(src)), "corr_tile_config")
+        names = {0: "narrow", 1: "wide", 2: "pair"}
+        sources = {0: "forced", 1: "rule", 2: "timed", 3: "memory", 4: "file"}
+        return {"variant": names[v.value], "tail": names[t.value], "layout": l.value,
+                "source": sources[src.value]}
+
+    def tune_results(self, batch: bool = False):
+        """``corr_tune_results``: [(variant, tail, layout), ms] of the
+        candidates the autotuner timed."""
+        n = self.L.corr_tune_results(self.h, int(batch), 0, None, None)
+        cfg = (ctypes.c_int * (3 * max(n, 1)))()
+        ms = (ctypes.c_float * max(n, 1))()
+        self.L.corr_tune_results(self.h, int(batch), n, cfg, ms)
+        names = {0: "narrow", 1: "wide", 2: "pair"}
+        return [((names[cfg[3 * i]], names[cfg[3 * i + 1]], cfg[3 * i + 2]), ms[i]) for i in range(n)]
 
     def batch_tile_variant(self) -> Optional[str]:
         """Tile variant of the current ragged batch (None before any)."""

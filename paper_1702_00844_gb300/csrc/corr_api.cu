@@ -2,10 +2,16 @@
 // kernel dispatch. See include/corr.h for the contract of every entry point.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cerrno>
+#include <fcntl.h>
 #include <map>
+#include <string>
+#include <sys/stat.h>
+#include <unistd.h>
 #include <tuple>
 #include <cstdio>
 #include <cstdlib>
@@ -18,6 +24,17 @@
 #include "corr_internal.h"
 
 using namespace corr;
+
+// A tile configuration of the tensor path: the variant of the main work
+// list, the variant of the tail list (pair variant with an odd block count:
+// narrow tiles for the last block column, or wide tiles for block 0's row)
+// and the kernel layout (int8 pair tiles of two pols: 0 with staged
+// epilogue groups, 1 with the six-stage operand ring).
+struct TileCfg {
+    int variant = TC_NARROW;
+    int tail = TC_WIDE;
+    int layout = 0;
+};
 
 struct corr_plan {
     corr_desc_t d{};
@@ -34,10 +51,12 @@ struct corr_plan {
     // tensor path (single problem)
     int4 *d_items = nullptr;   // main list, then the tail list (pair variant)
     int n_items = 0;           // main list
-    int n_tail = 0;            // tail list (narrow tiles of an odd last block column)
-    int tc_variant = TC_NARROW;
+    int n_tail = 0;            // tail list (pair variant, odd block count)
+    TileCfg tc;                // tile configuration (autotuned in corr_create)
+    int tune_source = 0;       // how it was chosen (corr_tile_config)
     int pair_clusters = 0;     // clusters of the pair variant resident at once (0: unavailable)
-    float tune_ms[TC_N_VARIANTS] = {0.f, 0.f, 0.f};
+    std::vector<TileCfg> tune_cfgs;  // candidates timed in corr_create, and their times
+    std::vector<float> tune_ms;
     // int8 power check / redo list (single problem and batches): state =
     // {count, done} of the main and the tail list, then one mark per item
     int *d_redo_state = nullptr;
@@ -50,9 +69,10 @@ struct corr_plan {
     int4 *d_bitems = nullptr;
     int n_bitems = 0;
     int n_btail = 0;
-    int b_variant = TC_NARROW;
+    TileCfg bc;                // tile configuration of the current batch
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // corr_set_kernel_events (not owned)
-    float b_tune_ms[TC_N_VARIANTS] = {};  // batch variant timings (0: not timed)
+    std::vector<TileCfg> b_tune_cfgs;  // batch candidates timed and their best times
+    std::vector<float> b_tune_ms;
     // host-buffer streaming (CORR_FLAG_HOST_IO)
     int chunk_units = 0;
     void *d_stage_in[2] = {nullptr, nullptr};
@@ -200,21 +220,34 @@ size_t out_unit_bytes(const corr_desc_t &d)
 // block rb and column blocks cb0..cb0+ncb-1 of 64 stations, rb <= cb0.
 // narrow: every (rb, cb) with rb <= cb; wide: column blocks taken in pairs
 // from the row block onward (the last one alone if the count is odd); pair:
-// row blocks {rb, rb+1} x column blocks {cb0, cb0+1} for even rb <= cb0 over
-// the first 2*floor(nb/2) blocks, and, when the block count nb is odd, the
-// last block column as narrow tiles (rb, nb-1) in *tail (a pair tile there
-// would hold a block without stations). Items are unit-major.
-std::vector<int4> tc_items_for(int prob, int S, int units, int variant, std::vector<int4> *tail)
+// row blocks {rb, rb+1} x column blocks {cb0, cb0+1} for rb <= cb0 over an
+// even number of blocks. When the block count nb is odd one block is left
+// over (a pair tile there would hold a block without stations), and its
+// tiles go to *tail: with tail_kind TC_WIDE the pair tiles cover blocks
+// 1 .. nb-1 and block 0's row goes to the tail as wide tiles, the diagonal
+// tile (0, 0) and then (0, {c, c+1}) for c = 1, 3, ... (fewer tiles, each
+// with N = 256); with TC_NARROW the pair tiles cover blocks 0 .. nb-2 and
+// the last block column goes to the tail as narrow tiles (nb of them, with
+// double-buffered accumulators). Items are unit-major.
+std::vector<int4> tc_items_for(int prob, int S, int units, int variant, std::vector<int4> *tail,
+                               int tail_kind = TC_WIDE)
 {
     std::vector<int4> v;
     const int nb = tc_blocks(S);
     for (int u = 0; u < units; ++u) {
-        if (variant == TC_PAIR) {
-            const int nbe = nb & ~1;
-            for (int rb = 0; rb < nbe; rb += 2)
-                for (int cb = rb; cb < nbe; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
-            if (nb & 1)
-                for (int rb = 0; rb < nb; ++rb) tail->push_back(make_int4(prob, u, rb, (nb - 1) | (1 << 16)));
+        if (variant == TC_PAIR && (nb & 1) && tail_kind == TC_NARROW) {
+            // pair tiles over blocks 0 .. nb-2, the last block column as narrow tiles
+            for (int rb = 0; rb + 1 < nb; rb += 2)
+                for (int cb = rb; cb + 1 < nb; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
+            for (int rb = 0; rb < nb; ++rb) tail->push_back(make_int4(prob, u, rb, (nb - 1) | (1 << 16)));
+        } else if (variant == TC_PAIR) {
+            const int b0 = nb & 1;   // first block of the pair tiles
+            for (int rb = b0; rb < nb; rb += 2)
+                for (int cb = rb; cb < nb; cb += 2) v.push_back(make_int4(prob, u, rb, cb | (2 << 16)));
+            if (b0) {
+                tail->push_back(make_int4(prob, u, 0, 0 | (1 << 16)));
+                for (int cb = 1; cb < nb; cb += 2) tail->push_back(make_int4(prob, u, 0, cb | (2 << 16)));
+            }
         } else if (variant == TC_WIDE) {
             for (int rb = 0; rb < nb; ++rb)
                 for (int cb = rb; cb < nb; cb += 2) {
@@ -295,7 +328,7 @@ int tc_grid_for(const corr_plan *h, int variant, int n)
 
 // One item list in one tile variant. The int8 redo list of this launch uses
 // the plan's redo entries [redo_off, redo_off + p.n_items) and counter `ctr`.
-corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max_T, int redo_off,
+corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int layout, int max_T, int redo_off,
                        int ctr, cudaStream_t s)
 {
     if (variant == TC_PAIR && h->pair_clusters < 1) {
@@ -308,10 +341,14 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
     // measurement hook (corr_set_kernel_events): around the main list's
     // first launch only
     const bool mark = ctr == 0 && h->ev_k0 && h->ev_k1;
+    // The tail list (ctr 1) reads nothing the main list's launches write:
+    // its first launch is a programmatic dependent that needs no wait, so
+    // its CTAs take SMs as soon as the main launch's CTAs leave them.
+    const bool pdl = ctr == 1;
     if (!checked) {
         p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
         if (mark) cudaEventRecord(h->ev_k0, s);
-        corr_status_t st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, p, grid, s));
+        corr_status_t st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, p, grid, s, pdl, layout));
         if (mark) cudaEventRecord(h->ev_k1, s);
         return st;
     }
@@ -327,7 +364,7 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
     a.redo_count = count;
     a.redo_done = nullptr;
     if (mark) cudaEventRecord(h->ev_k0, s);
-    corr_status_t st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s));
+    corr_status_t st = cuda_status(tc_launch(dtype, variant, h->d.n_pols, a, grid, s, pdl, layout));
     if (mark) cudaEventRecord(h->ev_k1, s);
     if (st != CORR_OK) return st;
     // the chunked redo launch over the rejected items (usually none), as a
@@ -341,21 +378,22 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int max
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
     b.redo_done = count + 1;
-    return cuda_status(tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s, true));
+    return cuda_status(
+        tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s, true, layout));
 }
 
-// The main list of p in `variant`, then (pair variant) the n_tail narrow
-// tail items at `tail`.
-corr_status_t run_tensor(corr_plan *h, TcParams p, const int4 *tail, int n_tail, int dtype, int variant,
+// The main list of p in cfg.variant, then (pair variant) the n_tail tail
+// items at `tail` in cfg.tail.
+corr_status_t run_tensor(corr_plan *h, TcParams p, const int4 *tail, int n_tail, int dtype, const TileCfg &cfg,
                          int max_T, cudaStream_t s)
 {
     corr_status_t st = CORR_OK;
-    if (p.n_items > 0) st = run_list(h, p, dtype, variant, max_T, 0, 0, s);
+    if (p.n_items > 0) st = run_list(h, p, dtype, cfg.variant, cfg.layout, max_T, 0, 0, s);
     if (st == CORR_OK && n_tail > 0) {
         TcParams q = p;
         q.items = tail;
         q.n_items = n_tail;
-        st = run_list(h, q, dtype, TC_NARROW, max_T, p.n_items, 1, s);
+        st = run_list(h, q, dtype, cfg.tail, 0, max_T, p.n_items, 1, s);
     }
     return st;
 }
@@ -395,7 +433,7 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
     return run_tensor(h, p, h->d_items + h->n_items, (int)((long long)h->n_tail / all_units * units),
-                      d.dtype, h->tc_variant, d.n_samples, s);
+                      d.dtype, h->tc, d.n_samples, s);
 }
 
 corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cudaStream_t s)
@@ -405,12 +443,22 @@ corr_status_t launch_correlate(corr_plan *h, const void *d_in, void *d_out, cuda
 
 
 // ------------------------------------------------------------------ autotuner
-// The tile variant of the tensor path is chosen per (device, dtype, pols, S,
-// T, units) by
-// timing the variants once on zero-filled samples of the plan's shape (its
-// own size up to 2 GB), unless CORR_TC_VARIANT=
-// narrow|wide|pair forces one or CORR_FLAG_NO_AUTOTUNE asks for the
-// heuristic (pair from 128 stations). Choices are cached for the process.
+// The tile configuration of the tensor path (variant, tail kind, kernel
+// layout) is chosen per (device, dtype, pols, S, T, units):
+//  1. CORR_TC_VARIANT=narrow|wide|pair, CORR_TC_TAIL=narrow|wide and
+//     CORR_TC_LAYOUT=0|1 force parts of it (the rest by the size rule);
+//  2. CORR_FLAG_NO_AUTOTUNE (or T = 0) takes the size rule: pair tiles from
+//     128 stations, a wide tail from 5 blocks, layout 0;
+//  3. otherwise a choice cached in this process, or in the cache file, is
+//     used; else the candidates the cost model keeps are timed on seeded
+//     non-zero samples of the plan's shape and the fastest is kept (in
+//     memory and appended to the cache file).
+// The cache file is CORR_TUNE_CACHE if set ("off": none), else
+// $XDG_CACHE_HOME/corr_gb300/tune.txt or ~/.cache/corr_gb300/tune.txt. A
+// line holds the build of this library, the GPU's name and SM count, the
+// shape and the choice; lines of other builds are ignored.
+enum { TUNE_FORCED = 0, TUNE_RULE = 1, TUNE_TIMED = 2, TUNE_MEMORY = 3, TUNE_FILE = 4 };
+
 struct TuneKey {
     int dev, dtype, npol, S, T;
     long long units; // the choice depends on the waves of work items too
@@ -420,11 +468,12 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, TileCfg> g_tune_cache;
+const char *const kBuildId = __DATE__ " " __TIME__;
 
-int forced_variant()
+int env_variant(const char *name)
 {
-    const char *e = std::getenv("CORR_TC_VARIANT");
+    const char *e = std::getenv(name);
     if (!e) return -1;
     if (std::strcmp(e, "wide") == 0) return TC_WIDE;
     if (std::strcmp(e, "narrow") == 0) return TC_NARROW;
@@ -432,11 +481,144 @@ int forced_variant()
     return -1;
 }
 
-corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, const void *d_in,
-                           void *d_out, float *ms_out)
+int forced_variant() { return env_variant("CORR_TC_VARIANT"); }
+
+int forced_layout()
+{
+    const char *e = std::getenv("CORR_TC_LAYOUT");
+    if (!e) return -1;
+    return std::atoi(e) == 1 ? 1 : 0;
+}
+
+// Layout 1 exists for the int8 pair kernel of two pols only.
+bool has_layouts(const corr_desc_t &d) { return d.dtype == CORR_CI8 && d.n_pols == 2; }
+
+// Size rule for S (item) stations: pair tiles from 128 stations when they fit
+// (wide otherwise), narrow below; the wide tail from 5 blocks (at 3 blocks
+// the narrow tail's double-buffered accumulators measured faster).
+TileCfg rule_cfg(const corr_plan *h, int S_items)
+{
+    TileCfg c;
+    c.variant = S_items >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
+    c.tail = tc_blocks(S_items) >= 5 ? TC_WIDE : TC_NARROW;
+    c.layout = 0;
+    return c;
+}
+
+TileCfg apply_forced(const corr_plan *h, TileCfg c, bool *any)
+{
+    const int v = forced_variant(), t = env_variant("CORR_TC_TAIL"), l = forced_layout();
+    *any = v >= 0 || t >= 0 || l >= 0;
+    if (v >= 0) c.variant = (v == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : v;
+    if (t == TC_NARROW || t == TC_WIDE) c.tail = t;
+    if (l >= 0) c.layout = has_layouts(h->d) ? l : 0;
+    return c;
+}
+
+// Cost model of a tile configuration (in the spirit of Section 2's Table 1:
+// work per tile against the operand bytes it moves). A tile's MMAs read
+// their operands from shared memory: per tensor-core clock 128 B (narrow,
+// M = N = 128), 96 B (wide, N = 256) or 64 B per SM (pair, M = 256 over two
+// SMs), of which the tensor core sustains about 72 B/clk (measured MMA-only
+// rates: 60 %, 75 %, about 100 %). Predicted time = SM-time of the computed
+// station pairs (the lower triangles of diagonal tiles included) over the
+// SM count; used only to prune candidates before timing.
+double tile_eff(int v) { return v == TC_PAIR ? 1.0 : v == TC_WIDE ? 0.75 : 0.5625; }
+
+double model_items(const std::vector<int4> &items, int variant, int S_items)
+{
+    double w = 0;
+    for (const int4 &it : items) {
+        const int ncb = it.w >> 16, cb0 = it.w & 0xFFFF;
+        if (variant == TC_PAIR) {
+            w += 2.0 * 64.0 * 128.0 / tile_eff(TC_PAIR);
+        } else {
+            const int last = std::min(TC_SIDE, S_items - (cb0 + ncb - 1) * TC_SIDE);
+            const int cols = (ncb - 1) * TC_SIDE + ((2 * last + 15) / 16) * 8;
+            w += 64.0 * cols / tile_eff(variant);
+        }
+    }
+    return w;
+}
+
+double model_cost(const corr_plan *h, int S_items, int T, long long units, const TileCfg &c)
 {
     std::vector<int4> tail;
-    std::vector<int4> items = tc_items_for(0, item_stations(S, h->d.n_pols), units, variant, &tail);
+    const std::vector<int4> items = tc_items_for(0, S_items, 1, c.variant, &tail, c.tail);
+    const double w = model_items(items, c.variant, S_items) + model_items(tail, c.tail, S_items);
+    return w * (double)T * (double)units / std::max(1, h->sm_count);
+}
+
+// Candidates for S (item) stations: narrow, wide and pair tiles (both tail
+// kinds when the block count is odd, both layouts where there are two),
+// pruned to those the cost model puts within 1.3x of the best.
+std::vector<TileCfg> tune_candidates(const corr_plan *h, const std::vector<std::tuple<int, int, long long>> &shapes)
+{
+    std::vector<TileCfg> all;
+    bool odd = false;
+    for (const auto &sh : shapes) odd |= (tc_blocks(std::get<0>(sh)) & 1) != 0;
+    for (int v = 0; v < TC_N_VARIANTS; ++v) {
+        if (v == TC_PAIR && h->pair_clusters < 1) continue;
+        for (int t : {TC_WIDE, TC_NARROW}) {
+            if (v != TC_PAIR && t != TC_WIDE) continue;   // the tail kind applies to pair tiles only
+            if (v == TC_PAIR && !odd && t != TC_WIDE) continue;
+            for (int l = 0; l < (v == TC_PAIR && has_layouts(h->d) ? 2 : 1); ++l) {
+                TileCfg c;
+                c.variant = v;
+                c.tail = t;
+                c.layout = l;
+                all.push_back(c);
+            }
+        }
+    }
+    std::vector<double> cost(all.size(), 0.0);
+    double best = 1e300;
+    for (size_t i = 0; i < all.size(); ++i) {
+        for (const auto &sh : shapes)
+            cost[i] += model_cost(h, std::get<0>(sh), std::get<1>(sh), std::get<2>(sh), all[i]);
+        best = std::min(best, cost[i]);
+    }
+    std::vector<TileCfg> keep;
+    for (size_t i = 0; i < all.size(); ++i)
+        if (cost[i] <= 1.3 * best) keep.push_back(all[i]);
+    return keep;
+}
+
+// Seeded non-zero samples for the timing runs: a counter-based 32-bit hash
+// (Wellons' "lowbias32": xorshift-multiply rounds) of each word's index;
+// int8 samples uniform in [-55, 55] (the rms of N(0, 32^2) samples, so that
+// the station power check behaves as on such data), f16 samples uniform in
+// [-1, 1).
+__global__ void tune_fill_kernel(uint32_t *w, size_t n, int f16, uint32_t seed)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 0x9E3779B9u ^ seed;
+        x ^= x >> 16;
+        x *= 0x7feb352du;
+        x ^= x >> 15;
+        x *= 0x846ca68bu;
+        x ^= x >> 16;
+        uint32_t out = 0;
+        if (f16) {
+            for (int k = 0; k < 2; ++k) {
+                const float v = (float)((int)((x >> (16 * k)) & 0x3FFu) - 512) / 512.0f;
+                out |= (uint32_t)__half_as_ushort(__float2half_rn(v)) << (16 * k);
+            }
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                const int v = (int)((x >> (8 * k)) & 0xFFu) % 111 - 55;
+                out |= (uint32_t)(v & 0xFF) << (8 * k);
+            }
+        }
+        w[i] = out;
+    }
+}
+
+corr_status_t time_config(corr_plan *h, const TileCfg &cfg, int S, int T, int units, const void *d_in,
+                          void *d_out, float *ms_out)
+{
+    std::vector<int4> tail;
+    std::vector<int4> items = tc_items_for(0, item_stations(S, h->d.n_pols), units, cfg.variant, &tail, cfg.tail);
     const int n_main = (int)items.size(), n_tail = (int)tail.size();
     items.insert(items.end(), tail.begin(), tail.end());
     int4 *d_items = nullptr;
@@ -457,11 +639,11 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
         if ((st = cuda_status(cudaEventCreate(&e0))) != CORR_OK) break;
         if ((st = cuda_status(cudaEventCreate(&e1))) != CORR_OK) break;
         for (int i = 0; i < 2 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, variant, T, 0);
+            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, cfg, T, 0);
         if (st != CORR_OK) break;
         cudaEventRecord(e0, 0);
         for (int i = 0; i < 3 && st == CORR_OK; ++i)
-            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, variant, T, 0);
+            st = run_tensor(h, p, d_items + n_main, n_tail, h->d.dtype, cfg, T, 0);
         cudaEventRecord(e1, 0);
         if (st != CORR_OK) break;
         if ((st = cuda_status(cudaEventSynchronize(e1))) != CORR_OK) break;
@@ -475,33 +657,124 @@ corr_status_t time_variant(corr_plan *h, int variant, int S, int T, int units, c
     return st;
 }
 
-corr_status_t tune_tensor_variant(corr_plan *h)
+std::string tune_cache_path()
+{
+    if (const char *e = std::getenv("CORR_TUNE_CACHE")) return std::strcmp(e, "off") == 0 ? std::string() : e;
+    std::string base;
+    if (const char *x = std::getenv("XDG_CACHE_HOME"); x && *x)
+        base = x;
+    else if (const char *home = std::getenv("HOME"); home && *home)
+        base = std::string(home) + "/.cache";
+    else
+        return std::string();
+    return base + "/corr_gb300/tune.txt";
+}
+
+// "<build> <gpu name> <SMs> <dtype> <pols> <S> <T> <units>" (spaces in the
+// build and GPU name become '_').
+std::string tune_line_key(const corr_plan *h)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, h->device);
+    std::string name = prop.name, build = kBuildId;
+    for (char &c : name) if (c == ' ') c = '_';
+    for (char &c : build) if (c == ' ') c = '_';
+    const corr_desc_t &d = h->d;
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s %s %d %d %d %d %d %lld", build.c_str(), name.c_str(), h->sm_count, (int)d.dtype,
+             d.n_pols, d.n_stations, d.n_samples, (long long)d.n_channels * d.n_integrations);
+    return buf;
+}
+
+bool tune_file_lookup(const corr_plan *h, TileCfg *out)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return false;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    const std::string key = tune_line_key(h);
+    char line[640];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        const size_t n = key.size();
+        if (std::strncmp(line, key.c_str(), n) != 0 || line[n] != ' ') continue;
+        int v = -1, t = -1, l = -1;
+        if (std::sscanf(line + n, "%d %d %d", &v, &t, &l) == 3 && v >= 0 && v < TC_N_VARIANTS &&
+            (t == TC_NARROW || t == TC_WIDE) && (l == 0 || l == 1) &&
+            !(v == TC_PAIR && h->pair_clusters < 1)) {
+            out->variant = v;
+            out->tail = t;
+            out->layout = has_layouts(h->d) ? l : 0;
+            found = true;   // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_file_append(const corr_plan *h, const TileCfg &c)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos && slash > 0) {
+        // create the directory (and, one level up, its parent) if missing
+        const std::string dir = path.substr(0, slash);
+        const size_t up = dir.rfind('/');
+        if (up != std::string::npos && up > 0) mkdir(dir.substr(0, up).c_str(), 0755);
+        mkdir(dir.c_str(), 0755);
+    }
+    const std::string line = tune_line_key(h) + " " + std::to_string(c.variant) + " " + std::to_string(c.tail) +
+                             " " + std::to_string(c.layout) + "\n";
+    // one write() of a short line to a file opened for appending
+    const int fd = open(path.c_str(), O_WRONLY | O_CREAT | O_APPEND, 0644);
+    if (fd < 0) return;
+    const ssize_t w = write(fd, line.data(), line.size());
+    (void)w;
+    close(fd);
+}
+
+corr_status_t tune_tensor_config(corr_plan *h)
 {
     const corr_desc_t &d = h->d;
-    const int f = forced_variant();
-    if (f >= 0) {
-        h->tc_variant = (f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f;
+    const int S_items = item_stations(d.n_stations, d.n_pols);
+    bool forced = false;
+    const TileCfg rule = rule_cfg(h, S_items);
+    const TileCfg f = apply_forced(h, rule, &forced);
+    if (forced) {
+        h->tc = f;
+        h->tune_source = TUNE_FORCED;
         return CORR_OK;
     }
     if ((d.flags & CORR_FLAG_NO_AUTOTUNE) || d.n_samples == 0) {
-        h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
+        h->tc = rule;
+        h->tune_source = TUNE_RULE;
         return CORR_OK;
     }
-    const TuneKey key{h->device, d.dtype, d.n_pols, d.n_stations, d.n_samples,
-                      (long long)d.n_channels * d.n_integrations};
+    const long long units = (long long)d.n_channels * d.n_integrations;
+    const TuneKey key{h->device, d.dtype, d.n_pols, d.n_stations, d.n_samples, units};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            h->tc_variant = it->second;
+            h->tc = it->second;
+            h->tune_source = TUNE_MEMORY;
             return CORR_OK;
         }
     }
-    const long long units = (long long)d.n_channels * d.n_integrations;
-    // The plan's own unit count, up to 2 GB of zero-filled samples and
-    // visibilities: the variants' wave quantisation at the real size decides
-    // (the pair variant splits its work over two launches). If that memory is
-    // not free, a quarter of it, and otherwise the heuristic choice.
+    TileCfg cached;
+    if (tune_file_lookup(h, &cached)) {
+        h->tc = cached;
+        h->tune_source = TUNE_FILE;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = cached;
+        return CORR_OK;
+    }
+    const std::vector<TileCfg> cands = tune_candidates(h, {std::make_tuple(S_items, d.n_samples, units)});
+    // The plan's own unit count, up to 2 GB of samples and visibilities: the
+    // configurations' wave quantisation at the real size decides (the pair
+    // variant splits its work over two launches). If that memory is not
+    // free, a quarter of it, and otherwise the size rule.
     const long long fit = std::max(1LL, (2048LL << 20) / (long long)(in_unit_bytes(d) + out_unit_bytes(d)));
     int su = (int)std::max(1LL, std::min(units, fit));
     void *d_in = nullptr, *d_out = nullptr;
@@ -515,24 +788,36 @@ corr_status_t tune_tensor_variant(corr_plan *h)
         su = std::max(1, su / 4);
     }
     if (!d_in || !d_out) {
-        h->tc_variant = d.n_stations >= 128 ? (h->pair_clusters > 0 ? TC_PAIR : TC_WIDE) : TC_NARROW;
+        h->tc = rule;
+        h->tune_source = TUNE_RULE;
         return CORR_OK;
     }
-    corr_status_t st = cuda_status(cudaMemset(d_in, 0, (size_t)su * in_unit_bytes(d)));
-    for (int v = 0; v < TC_N_VARIANTS && st == CORR_OK; ++v) {
-        h->tune_ms[v] = 0.f;
-        if (v == TC_PAIR && h->pair_clusters < 1) continue;
-        st = time_variant(h, v, d.n_stations, d.n_samples, su, d_in, d_out, &h->tune_ms[v]);
+    const size_t words = (size_t)su * in_unit_bytes(d) / 4;
+    tune_fill_kernel<<<std::max(1, 4 * h->sm_count), 256>>>(static_cast<uint32_t *>(d_in), words,
+                                                            d.dtype == CORR_CF16 ? 1 : 0, 1702844u);
+    corr_status_t st = cuda_status(cudaGetLastError());
+    h->tune_cfgs.clear();
+    h->tune_ms.clear();
+    for (const TileCfg &c : cands) {
+        if (st != CORR_OK) break;
+        float ms = 0.f;
+        st = time_config(h, c, d.n_stations, d.n_samples, su, d_in, d_out, &ms);
+        if (st == CORR_OK) {
+            h->tune_cfgs.push_back(c);
+            h->tune_ms.push_back(ms);
+        }
     }
     cudaFree(d_in);
     cudaFree(d_out);
     if (st != CORR_OK) return st;
-    int best = TC_NARROW;
-    for (int v = 1; v < TC_N_VARIANTS; ++v)
-        if (h->tune_ms[v] > 0.f && h->tune_ms[v] < h->tune_ms[best]) best = v;
-    h->tc_variant = best;
+    size_t best = 0;
+    for (size_t i = 1; i < h->tune_ms.size(); ++i)
+        if (h->tune_ms[i] < h->tune_ms[best]) best = i;
+    h->tc = h->tune_cfgs.empty() ? rule : h->tune_cfgs[best];
+    h->tune_source = TUNE_TIMED;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = h->tc_variant;
+    g_tune_cache[key] = h->tc;
+    tune_file_append(h, h->tc);
     return CORR_OK;
 }
 
@@ -567,6 +852,27 @@ void corr_tile_cost(int w, int h, long *flops, long *bytes, long *regs)
     if (flops) *flops = 32L * w * h;
     if (bytes) *bytes = 16L * (w + h);
     if (regs) *regs = 4L * (1 + std::min(w, h)) + 8L * w * h;
+}
+
+int corr_tc_schedule(int variant, int tail_kind, int n_stations, int cap, int *out)
+{
+    if (n_stations < 1 || variant < TC_NARROW || variant > TC_PAIR || cap < 0) return -1;
+    if (tail_kind != TC_NARROW && tail_kind != TC_WIDE) return -1;
+    std::vector<int4> tail;
+    const std::vector<int4> items = tc_items_for(0, n_stations, 1, variant, &tail, tail_kind);
+    const int n = (int)(items.size() + tail.size());
+    if (!out) return n;
+    if (n > cap) return -1;
+    int k = 0;
+    for (int t = 0; t < 2; ++t)
+        for (const int4 &it : t ? tail : items) {
+            out[4 * k + 0] = it.z;
+            out[4 * k + 1] = it.w & 0xFFFF;
+            out[4 * k + 2] = it.w >> 16;
+            out[4 * k + 3] = t;
+            ++k;
+        }
+    return n;
 }
 
 int corr_tc_tiles(int S)
@@ -662,10 +968,10 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
                                                                    out_unit_bytes(d)))) != CORR_OK)
                 break;
         } else {
-            if ((st = tune_tensor_variant(h)) != CORR_OK) break;
+            if ((st = tune_tensor_config(h)) != CORR_OK) break;
             std::vector<int4> tail;
             std::vector<int4> items =
-                tc_items_for(0, item_stations(d.n_stations, d.n_pols), (int)units, h->tc_variant, &tail);
+                tc_items_for(0, item_stations(d.n_stations, d.n_pols), (int)units, h->tc.variant, &tail, h->tc.tail);
             h->n_items = (int)items.size();
             h->n_tail = (int)tail.size();
             items.insert(items.end(), tail.begin(), tail.end());
@@ -774,7 +1080,7 @@ namespace {
 // Work list of a ragged batch in tile variant v: tiles of all sub-arrays,
 // heaviest (longest integration) first so that the static round-robin split
 // over the persistent CTAs ends evenly; the narrow tail items last.
-corr_status_t batch_items(corr_plan *h, int n_sub, const corr_subarray_t *subs, int v)
+corr_status_t batch_items(corr_plan *h, int n_sub, const corr_subarray_t *subs, const TileCfg &cfg)
 {
     std::vector<int4> items, tail;
     std::vector<int> T(n_sub);
@@ -782,7 +1088,7 @@ corr_status_t batch_items(corr_plan *h, int n_sub, const corr_subarray_t *subs, 
         T[i] = subs[i].n_samples;
         if (subs[i].n_samples == 0) continue;
         std::vector<int4> u = tc_items_for(i, item_stations(subs[i].n_stations, h->d.n_pols),
-                                           subs[i].n_channels, v, &tail);
+                                           subs[i].n_channels, cfg.variant, &tail, cfg.tail);
         items.insert(items.end(), u.begin(), u.end());
     }
     auto heavier = [&](const int4 &a, const int4 &b) { return T[a.x] > T[b.x]; };
@@ -813,7 +1119,7 @@ corr_status_t run_batch(corr_plan *h, int max_T, cudaStream_t st)
     p.n_items = h->n_bitems;
     p.err = h->d_err;
     p.wait_ns = h->wait_ns;
-    return run_tensor(h, p, h->d_bitems + h->n_bitems, h->n_btail, h->d.dtype, h->b_variant, max_T, st);
+    return run_tensor(h, p, h->d_bitems + h->n_bitems, h->n_btail, h->d.dtype, h->bc, max_T, st);
 }
 
 // One warm-up run and one timed run of the current batch work list.
@@ -878,48 +1184,60 @@ corr_status_t corr_correlate_batched(corr_handle_t h, int n_sub, const corr_suba
         if ((e = cuda_status(cudaMemcpy(h->d_bprobs, probs.data(), probs.size() * sizeof(TcProblem),
                                         cudaMemcpyHostToDevice))) != CORR_OK)
             return e;
-        // One tile variant serves the whole batch. Forced by CORR_TC_VARIANT;
-        // otherwise timed on this batch (two rounds; each run warms up once
-        // and times once; the sub-arrays' outputs are simply overwritten), unless the
-        // plan skips tuning or the stream is being captured, where pair (wide
-        // if pairs do not fit) is taken when most of the work is in
-        // sub-arrays of >= 128 stations.
-        const int f = forced_variant();
+        // One tile configuration serves the whole batch. Parts forced by
+        // CORR_TC_VARIANT / CORR_TC_TAIL / CORR_TC_LAYOUT; otherwise the
+        // candidates the cost model keeps are timed on this batch (two
+        // rounds; each run warms up once and times once; the sub-arrays'
+        // outputs are simply overwritten), unless the plan skips tuning or
+        // the stream is being captured, where the size rule decides: pair
+        // tiles (wide if pairs do not fit) when most of the work is in
+        // sub-arrays of >= 128 stations, with the wide tail.
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if ((e = cuda_status(cudaStreamIsCapturing(st, &cap))) != CORR_OK) return e;
         const int big_v = h->pair_clusters > 0 ? TC_PAIR : TC_WIDE;
-        for (int v = 0; v < TC_N_VARIANTS; ++v) h->b_tune_ms[v] = 0.f;
-        if (f >= 0) {
-            h->b_variant = (f == TC_PAIR && h->pair_clusters < 1) ? TC_WIDE : f;
-        } else {
-            double big = 0, all = 0;
-            for (int i = 0; i < n_sub; ++i) {
-                const double w = (double)n_baselines(subs[i].n_stations) * subs[i].n_samples *
-                                 subs[i].n_channels;
-                all += w;
-                if (subs[i].n_stations >= 128) big += w;
-            }
-            const int rule = big >= 0.5 * all ? big_v : TC_NARROW;
-            h->b_variant = rule;
-            if (!(h->d.flags & CORR_FLAG_NO_AUTOTUNE) && cap == cudaStreamCaptureStatusNone && max_T > 0) {
-                // two rounds over the variants, each variant's best time
-                // counts; within 2% of the best, the size rule's choice stays
-                for (int round = 0; round < 2; ++round)
-                    for (int v = 0; v < TC_N_VARIANTS; ++v) {
-                        if (v == TC_PAIR && h->pair_clusters < 1) continue;
-                        h->b_variant = v;
-                        if ((e = batch_items(h, n_sub, subs, v)) != CORR_OK) return e;
-                        float ms = 0.f;
-                        if ((e = time_batch(h, max_T, st, &ms)) != CORR_OK) return e;
-                        if (round == 0 || ms < h->b_tune_ms[v]) h->b_tune_ms[v] = ms;
-                    }
-                int best = rule;
-                for (int v = 0; v < TC_N_VARIANTS; ++v)
-                    if (h->b_tune_ms[v] > 0.f && h->b_tune_ms[v] < 0.98f * h->b_tune_ms[best]) best = v;
-                h->b_variant = best;
-            }
+        h->b_tune_cfgs.clear();
+        h->b_tune_ms.clear();
+        double big = 0, all = 0;
+        std::vector<std::tuple<int, int, long long>> shapes;
+        for (int i = 0; i < n_sub; ++i) {
+            const double w = (double)n_baselines(subs[i].n_stations) * subs[i].n_samples * subs[i].n_channels;
+            all += w;
+            if (subs[i].n_stations >= 128) big += w;
+            if (subs[i].n_samples > 0)
+                shapes.emplace_back(item_stations(subs[i].n_stations, h->d.n_pols), subs[i].n_samples,
+                                    (long long)subs[i].n_channels);
         }
-        if ((e = batch_items(h, n_sub, subs, h->b_variant)) != CORR_OK) return e;
+        TileCfg rule;
+        rule.variant = big >= 0.5 * all ? big_v : TC_NARROW;
+        rule.tail = TC_WIDE;
+        rule.layout = 0;
+        bool forced = false;
+        h->bc = apply_forced(h, rule, &forced);
+        if (!forced && !(h->d.flags & CORR_FLAG_NO_AUTOTUNE) && cap == cudaStreamCaptureStatusNone && max_T > 0) {
+            // two rounds over the candidates, each one's best time counts;
+            // within 2% of the best, the size rule's choice stays
+            const std::vector<TileCfg> cands = tune_candidates(h, shapes);
+            h->b_tune_cfgs = cands;
+            h->b_tune_ms.assign(cands.size(), 0.f);
+            for (int round = 0; round < 2; ++round)
+                for (size_t i = 0; i < cands.size(); ++i) {
+                    h->bc = cands[i];
+                    if ((e = batch_items(h, n_sub, subs, h->bc)) != CORR_OK) return e;
+                    float ms = 0.f;
+                    if ((e = time_batch(h, max_T, st, &ms)) != CORR_OK) return e;
+                    if (round == 0 || ms < h->b_tune_ms[i]) h->b_tune_ms[i] = ms;
+                }
+            size_t best = cands.size();
+            float rule_ms = 0.f;
+            for (size_t i = 0; i < cands.size(); ++i)
+                if (cands[i].variant == rule.variant && cands[i].tail == rule.tail && cands[i].layout == rule.layout)
+                    rule_ms = h->b_tune_ms[i];
+            for (size_t i = 0; i < cands.size(); ++i)
+                if (best == cands.size() || h->b_tune_ms[i] < h->b_tune_ms[best]) best = i;
+            h->bc = (rule_ms > 0.f && h->b_tune_ms[best] >= 0.98f * rule_ms) || best == cands.size() ? rule
+                                                                                                     : cands[best];
+        }
+        if ((e = batch_items(h, n_sub, subs, h->bc)) != CORR_OK) return e;
         h->batch_key.assign(subs, subs + n_sub);
     }
     for (int i = 0; i < n_sub; ++i)
@@ -1013,13 +1331,40 @@ corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_
 int corr_tile_variant(corr_handle_t h)
 {
     if (!h) return -1;
-    return h->path == CORR_PATH_TENSOR ? h->tc_variant : -1;
+    return h->path == CORR_PATH_TENSOR ? h->tc.variant : -1;
 }
 
 int corr_batch_tile_variant(corr_handle_t h)
 {
     if (!h || h->batch_key.empty()) return -1;
-    return h->b_variant;
+    return h->bc.variant;
+}
+
+corr_status_t corr_tile_config(corr_handle_t h, int *variant, int *tail, int *layout, int *source)
+{
+    if (!h || h->path != CORR_PATH_TENSOR) return CORR_ERR_INVALID_ARG;
+    if (variant) *variant = h->tc.variant;
+    if (tail) *tail = h->tc.tail;
+    if (layout) *layout = h->tc.layout;
+    if (source) *source = h->tune_source;
+    return CORR_OK;
+}
+
+int corr_tune_results(corr_handle_t h, int batch, int cap, int *cfg, float *ms)
+{
+    if (!h || cap < 0) return -1;
+    const std::vector<TileCfg> &c = batch ? h->b_tune_cfgs : h->tune_cfgs;
+    const std::vector<float> &t = batch ? h->b_tune_ms : h->tune_ms;
+    const int n = (int)c.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (cfg) {
+            cfg[3 * i + 0] = c[i].variant;
+            cfg[3 * i + 1] = c[i].tail;
+            cfg[3 * i + 2] = c[i].layout;
+        }
+        if (ms) ms[i] = t[i];
+    }
+    return n;
 }
 
 corr_status_t corr_set_kernel_events(corr_handle_t h, void *ev_start, void *ev_stop)

@@ -140,10 +140,13 @@ template <> struct Cfg<2, TC_PAIR> {
 #endif
 constexpr int STG_GROUP_BYTES = 8 * 512;  // per warp: 8 column stations x 32 rows x 16 B
 
-// Stage counts per (input type, tile variant, pols): OPS operand stages, RAW
-// raw-sample stages, STG staged epilogue groups per epilogue warp.
-template <int DT, int V, int NPOL> struct Lay {
-    static constexpr bool STAGED = V == TC_PAIR && NPOL == 2 && DT == 2 && CORR_TC_STG_I8 > 0;
+// Stage counts per (input type, tile variant, pols, layout): OPS operand
+// stages, RAW raw-sample stages, STG staged epilogue groups per epilogue
+// warp. Layout LY = 1 (int8 pair tiles of two pols only, a second
+// instantiation the autotuner can choose) keeps the six-stage operand ring
+// and stores every epilogue group directly.
+template <int DT, int V, int NPOL, int LY = 0> struct Lay {
+    static constexpr bool STAGED = V == TC_PAIR && NPOL == 2 && DT == 2 && LY == 0 && CORR_TC_STG_I8 > 0;
     static constexpr int STG = STAGED ? CORR_TC_STG_I8 : 0;
     static constexpr int OPS = STAGED ? CORR_TC_OPS_STG_I8 : Cfg<DT, V>::OPS;
     static constexpr int RAW = Cfg<DT, V>::RAW;
@@ -157,9 +160,9 @@ template <int DT, int V> __host__ __device__ constexpr int raw_stage_bytes()
 {
     return (1 + Cfg<DT, V>::MAXB) * RawBytes<DT>::value * N_PRODUCERS;
 }
-template <int DT, int V, int NPOL> __host__ __device__ constexpr int smem_bytes()
+template <int DT, int V, int NPOL, int LY = 0> __host__ __device__ constexpr int smem_bytes()
 {
-    using L = Lay<DT, V, NPOL>;
+    using L = Lay<DT, V, NPOL, LY>;
     return L::OPS * stage_bytes<DT, V>() + L::RAW * raw_stage_bytes<DT, V>() +
            L::STG * 4 * STG_GROUP_BYTES;
 }
@@ -174,19 +177,20 @@ struct Bars {
     int abort_flag;
 };
 
-template <int DT, int V, int NPOL> constexpr bool cfg_ok()
+template <int DT, int V, int NPOL, int LY = 0> constexpr bool cfg_ok()
 {
-    using L = Lay<DT, V, NPOL>;
+    using L = Lay<DT, V, NPOL, LY>;
     return L::OPS >= 2 && L::OPS <= MAX_OPS && (L::RAW >= 2 || (L::RAW == 0 && DT == 2)) &&
            L::STG >= 0 && L::STG <= 16 &&
-           smem_bytes<DT, V, NPOL>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
+           smem_bytes<DT, V, NPOL, LY>() + (int)sizeof(Bars) + 1024 <= 227 * 1024;
 }
 template <int DT> constexpr bool cfg_ok_dt()
 {
     return cfg_ok<DT, TC_NARROW, 1>() && cfg_ok<DT, TC_NARROW, 2>() && cfg_ok<DT, TC_WIDE, 1>() &&
            cfg_ok<DT, TC_WIDE, 2>() && cfg_ok<DT, TC_PAIR, 1>() && cfg_ok<DT, TC_PAIR, 2>();
 }
-static_assert(cfg_ok_dt<1>() && cfg_ok_dt<2>(), "stage counts must fit the barrier arrays and shared memory");
+static_assert(cfg_ok_dt<1>() && cfg_ok_dt<2>() && cfg_ok<2, TC_PAIR, 2, 1>(),
+              "stage counts must fit the barrier arrays and shared memory");
 
 template <int DT> struct Raw;          // raw samples of 8 times of one station
 template <> struct Raw<1> { uint4 v[4]; }; // complex f16 x 2 pols: 64 bytes
@@ -572,10 +576,10 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
 // 2m and 2m+1 take the places of the two pols of "pseudo-station" m, so the
 // tiles, the schedule (over pseudo-stations) and the MMAs are those of the
 // two-pol case and only the sample copies and the output mapping differ.
-template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
+template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void tc_correlate_body(const TcParams &p)
 {
     using C = Cfg<DT, V>;
-    using L = Lay<DT, V, NPOL>;
+    using L = Lay<DT, V, NPOL, LY>;
     constexpr bool PAIR = V == TC_PAIR;
     constexpr bool N256 = V != TC_NARROW;          // tiles of two column blocks
     constexpr int OPS = L::OPS;
@@ -591,7 +595,7 @@ template <int DT, int V, int NPOL> __device__ __forceinline__ void tc_correlate_
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t tiles_u32 = smem_u32(smem);
     const uint32_t raw_base = tiles_u32 + OPS * STAGE;
-    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, V, NPOL>());
+    Bars *bars = reinterpret_cast<Bars *>(smem + smem_bytes<DT, V, NPOL, LY>());
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x;
@@ -1105,31 +1109,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_correlate_kernel(const __gri
     tc_correlate_body<DT, V, NPOL>(p);
 }
 
-template <int DT, int NPOL>
+template <int DT, int NPOL, int LY>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     tc_pair_kernel(const __grid_constant__ TcParams p)
 {
-    tc_correlate_body<DT, TC_PAIR, NPOL>(p);
+    tc_correlate_body<DT, TC_PAIR, NPOL, LY>(p);
 }
 
-template <int DT, int V, int NPOL> const void *kernel_ptr()
+template <int DT, int V, int NPOL, int LY> const void *kernel_ptr()
 {
     if constexpr (V == TC_PAIR)
-        return reinterpret_cast<const void *>(&tc_pair_kernel<DT, NPOL>);
+        return reinterpret_cast<const void *>(&tc_pair_kernel<DT, NPOL, LY>);
     else
         return reinterpret_cast<const void *>(&tc_correlate_kernel<DT, V, NPOL>);
 }
 
-template <int DT, int V, int NPOL> size_t smem_total()
+template <int DT, int V, int NPOL, int LY> size_t smem_total()
 {
-    return (size_t)smem_bytes<DT, V, NPOL>() + sizeof(Bars) + 1024;
+    return (size_t)smem_bytes<DT, V, NPOL, LY>() + sizeof(Bars) + 1024;
 }
 
-template <int DT, int V, int NPOL>
+template <int DT, int V, int NPOL, int LY>
 cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, bool pdl)
 {
-    const size_t smem = smem_total<DT, V, NPOL>();
-    cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V, NPOL>(),
+    const size_t smem = smem_total<DT, V, NPOL, LY>();
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr<DT, V, NPOL, LY>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (pdl) {
@@ -1144,46 +1148,53 @@ cudaError_t launch_one(const TcParams &p, int grid, cudaStream_t s, bool pdl)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         if constexpr (V == TC_PAIR)
-            return cudaLaunchKernelEx(&cfg, tc_pair_kernel<DT, NPOL>, p);
+            return cudaLaunchKernelEx(&cfg, tc_pair_kernel<DT, NPOL, LY>, p);
         else
             return cudaLaunchKernelEx(&cfg, tc_correlate_kernel<DT, V, NPOL>, p);
     }
     if constexpr (V == TC_PAIR)
-        tc_pair_kernel<DT, NPOL><<<grid, TC_THREADS, smem, s>>>(p);
+        tc_pair_kernel<DT, NPOL, LY><<<grid, TC_THREADS, smem, s>>>(p);
     else
         tc_correlate_kernel<DT, V, NPOL><<<grid, TC_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int DT, int NPOL>
-cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s, bool pdl)
+cudaError_t launch_dt(int variant, const TcParams &p, int grid, cudaStream_t s, bool pdl, int layout)
 {
-    if (variant == TC_PAIR) return launch_one<DT, TC_PAIR, NPOL>(p, grid, s, pdl);
-    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE, NPOL>(p, grid, s, pdl);
-    return launch_one<DT, TC_NARROW, NPOL>(p, grid, s, pdl);
+    if (variant == TC_PAIR) {
+        if constexpr (DT == 2 && NPOL == 2)
+            if (layout == 1) return launch_one<DT, TC_PAIR, NPOL, 1>(p, grid, s, pdl);
+        return launch_one<DT, TC_PAIR, NPOL, 0>(p, grid, s, pdl);
+    }
+    if (variant == TC_WIDE) return launch_one<DT, TC_WIDE, NPOL, 0>(p, grid, s, pdl);
+    return launch_one<DT, TC_NARROW, NPOL, 0>(p, grid, s, pdl);
 }
 
 template <int DT> cudaError_t pair_clusters_dt(int *n)
 {
-    const size_t smem = smem_total<DT, TC_PAIR, 2>();
-    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT, 2>,
+    const size_t smem = smem_total<DT, TC_PAIR, 2, 0>();
+    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<DT, 2, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, 1, 1);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    return cudaOccupancyMaxActiveClusters(n, tc_pair_kernel<DT, 2>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, tc_pair_kernel<DT, 2, 0>, &cfg);
 }
 
 } // namespace
 
-cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s, bool pdl)
+cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s, bool pdl,
+                      int layout)
 {
     if (variant == TC_PAIR && (grid < 2 || grid % 2 != 0)) return cudaErrorInvalidValue;
     if (npol == 1)
-        return dtype == 1 ? launch_dt<1, 1>(variant, p, grid, s, pdl) : launch_dt<2, 1>(variant, p, grid, s, pdl);
-    return dtype == 1 ? launch_dt<1, 2>(variant, p, grid, s, pdl) : launch_dt<2, 2>(variant, p, grid, s, pdl);
+        return dtype == 1 ? launch_dt<1, 1>(variant, p, grid, s, pdl, layout)
+                          : launch_dt<2, 1>(variant, p, grid, s, pdl, layout);
+    return dtype == 1 ? launch_dt<1, 2>(variant, p, grid, s, pdl, layout)
+                      : launch_dt<2, 2>(variant, p, grid, s, pdl, layout);
 }
 
 cudaError_t tc_pair_max_clusters(int dtype, int *n)

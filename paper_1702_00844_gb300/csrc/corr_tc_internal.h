@@ -59,8 +59,11 @@ constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 // pdl: launched as a programmatic dependent of the previous kernel on the
 // stream (the redo launch; the kernel waits for that kernel's completion
 // before it reads the redo count).
+// layout: 0, or 1 for the int8 pair kernel of two pols in its second
+// instantiation (six operand stages, no staged epilogue groups); ignored
+// elsewhere.
 cudaError_t tc_launch(int dtype, int variant, int npol, const TcParams &p, int grid, cudaStream_t s,
-                      bool pdl = false);
+                      bool pdl = false, int layout = 0);
 // Clusters of the pair variant that fit on the device at once.
 cudaError_t tc_pair_max_clusters(int dtype, int *n);
 

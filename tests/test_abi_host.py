@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -66,6 +68,50 @@ def test_tc_tile_schedule_covers_triangle(L):
             for s2 in range(c * 64, min(S, c * 64 + 64)):
                 covered += max(0, min(s2, r * 64 + 63) - r * 64 + 1)
         assert covered == S * (S + 1) // 2
+
+
+def _schedule(L, variant, tail, S):
+    n = L.corr_tc_schedule(variant, tail, S, 0, None)
+    assert n > 0
+    buf = (ctypes.c_int * (4 * n))()
+    assert L.corr_tc_schedule(variant, tail, S, n - 1, buf) == -1          # too small
+    assert L.corr_tc_schedule(variant, tail, S, n, buf) == n
+    return [tuple(buf[4 * k:4 * k + 4]) for k in range(n)]
+
+
+@pytest.mark.parametrize("variant,tail", [(0, 1), (1, 1), (2, 0), (2, 1)])
+def test_tc_work_schedules_cover_each_baseline_once(L, variant, tail):
+    """Every tile configuration's work tiles (the pair variant's two lists
+    included, with either tail kind) hold each baseline s1 <= s2 of a channel
+    exactly once; blocks that hold no stations appear only where a pair tile
+    needs a partner row block."""
+    for S in (1, 40, 64, 65, 128, 129, 150, 192, 200, 256, 320, 576, 600):
+        nb = (S + 63) // 64
+        tiles = _schedule(L, variant, tail, S)
+        count = np.zeros((S, S), dtype=np.int64)
+        for rb, cb0, ncb, lst in tiles:
+            rows = [rb, rb + 1] if variant == 2 and lst == 0 else [rb]
+            cols = list(range(cb0, cb0 + ncb))
+            assert 1 <= ncb <= 2 and rb <= cb0 and cb0 + ncb <= nb
+            if variant != 2:
+                assert lst == 0
+            for r in rows:
+                for c in cols:
+                    lo1, hi1 = r * 64, min(S, r * 64 + 64)
+                    lo2, hi2 = c * 64, min(S, c * 64 + 64)
+                    if lo1 < hi1 and lo2 < hi2:
+                        count[lo1:hi1, lo2:hi2] += 1
+        upper = np.triu(np.ones((S, S), dtype=bool))
+        assert (count[upper] == 1).all(), (variant, tail, S)
+        if variant == 2:
+            second = [t for t in tiles if t[3] == 1]
+            if nb % 2 == 0:
+                assert second == []
+            elif tail == 1:   # block 0's row as wide tiles
+                assert second == [(0, 0, 1, 1)] + [(0, c, 2, 1) for c in range(1, nb, 2)]
+            else:             # the last block column as narrow tiles
+                assert second == [(r, nb - 1, 1, 1) for r in range(nb)]
+    assert L.corr_tc_schedule(2, 3, 64, 0, None) == -1   # unknown tail kind
 
 
 def test_fp32_subtile_schedule_covers_triangle(L):

@@ -16,13 +16,29 @@ pytestmark = pytest.mark.gpu
 
 
 VARIANTS = ["narrow", "wide", "pair"]
+# Tile configurations (variant, tail kind of the pair variant's second list,
+# kernel layout): the autotuner chooses among these.
+CONFIGS = {"narrow": ("narrow", None, None), "wide": ("wide", None, None),
+           "pair": ("pair", None, None), "pair-narrow-tail": ("pair", "narrow", None),
+           "pair-wide-tail": ("pair", "wide", None), "pair-layout1": ("pair", None, "1")}
 
 
-@pytest.fixture(params=VARIANTS)
+def force_config(monkeypatch, name):
+    v, tail, layout = CONFIGS[name]
+    monkeypatch.setenv("CORR_TC_VARIANT", v)
+    for key, val in (("CORR_TC_TAIL", tail), ("CORR_TC_LAYOUT", layout)):
+        if val is None:
+            monkeypatch.delenv(key, raising=False)
+        else:
+            monkeypatch.setenv(key, val)
+    return v
+
+
+@pytest.fixture(params=list(CONFIGS))
 def variant(request, monkeypatch):
-    """Forces the tile variant of the plans a test creates."""
-    monkeypatch.setenv("CORR_TC_VARIANT", request.param)
-    return request.param
+    """Forces the tile configuration of the plans a test creates; returns its
+    variant."""
+    return force_config(monkeypatch, request.param)
 
 
 def run_tc(x: np.ndarray, S, C, T, dtype, I=1, expect_variant=None):
@@ -89,10 +105,11 @@ def test_int8_adversarial_extremes_chunk_fold(T, variant):
     exact_int(out, signs)
 
 
-@pytest.mark.parametrize("variant", ["pair"], indirect=True)
+@pytest.mark.parametrize("variant", ["pair-narrow-tail", "pair-wide-tail", "pair-layout1"], indirect=True)
 def test_int8_extremes_odd_block_count_pair_and_tail(variant):
-    """Three 64-station blocks with the pair variant: pair tiles over the first
-    two blocks and narrow tiles for the last block column, in two launches
+    """Three 64-station blocks with the pair variant: pair tiles over two
+    blocks and the third block's tiles in a second list (narrow tiles for
+    the last block column, or wide tiles for block 0's row), in two launches
     with their own redo lists. All-(+-127) samples over 1500 samples make
     every tile of both lists fail the power check and take its chunked redo."""
     S, C, T = 150, 2, 1500
@@ -119,12 +136,13 @@ def test_autotuner_picks_a_variant_and_variants_agree(monkeypatch):
     from paper_1702_00844_gb300 import Plan
     S, T, C = 190, 96, 3
     x8 = synth.int8_normal(synth.rng(64), (C, S, T, 2))
-    monkeypatch.delenv("CORR_TC_VARIANT", raising=False)
+    for key in ("CORR_TC_VARIANT", "CORR_TC_TAIL", "CORR_TC_LAYOUT"):
+        monkeypatch.delenv(key, raising=False)
     plan = Plan(S, C, T, dtype="ci8", path="tensor")
     assert plan.tile_variant() in VARIANTS
     outs = []
-    for v in VARIANTS:
-        monkeypatch.setenv("CORR_TC_VARIANT", v)
+    for name in CONFIGS:
+        v = force_config(monkeypatch, name)
         outs.append(to_numpy_int(run_tc(x8, S, C, T, "ci8", expect_variant=v)))
     for o in outs[1:]:
         np.testing.assert_array_equal(outs[0], o)
