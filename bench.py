@@ -216,6 +216,36 @@ def cpu_baseline(target_s: float = 12.0):
                       f"1024 samples each), FP64, {dt:.1f} s"}
 
 
+def cpu_fp32_correlator(target_s: float = 6.0):
+    """The multithreaded FP32 CPU correlator (Section 4.1's design) on the
+    precision workload's samples as complex64: channels sized from a first
+    timing on one channel per thread for about target_s, up to all 480."""
+    import numpy as np
+
+    import cpu_baseline
+    import synth
+    nthr = max(1, cpu_baseline.threads())
+
+    def samples(n):   # the first n channels, (n, S, T, 2) complex64
+        x = synth.precision(channels=list(range(n)))["x"]
+        return (x[..., 0].astype(np.float32) + 1j * x[..., 1].astype(np.float32)).astype(np.complex64)
+
+    xc = samples(nthr)
+    cpu_baseline.correlate(xc)                       # warm-up
+    t0 = time.perf_counter()
+    cpu_baseline.correlate(xc)
+    per_channel = max(time.perf_counter() - t0, 1e-4) / nthr
+    n = int(min(C3, max(nthr, target_s / per_channel)))
+    xc = samples(n)
+    t0 = time.perf_counter()
+    cpu_baseline.correlate(xc)
+    dt = time.perf_counter() - t0
+    return {"value": ops_of(S3, T3, n) / dt / 1e12, "unit": UNIT, "cores": nthr,
+            "kind": "multithreaded FP32 CPU correlator (2x2 station tiles, time loop vectorised, "
+                    "Section 4.1 design)",
+            "sample": f"{n} of 480 channels of the precision workload as complex64, {dt:.1f} s"}
+
+
 # ---------------------------------------------------------------- reference
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -540,6 +570,7 @@ def run_ours(args):
         line["paths"]["tensor_int8_vs_fp32_same_samples"] = value / fp32
     if rank == 0 and world == 1 and not args.no_cpu and wl == "precision":
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_fp32_correlator"] = cpu_fp32_correlator()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
