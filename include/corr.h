@@ -169,7 +169,14 @@ corr_status_t corr_gain_loss(corr_handle_t h, const void *d_raw_vis, const void 
  *       (d_in must then be 16-byte aligned, as for corr_correlate);
  *   d_loss (nullable): receives L.
  * Complex buffers must be 8-byte aligned, d_loss and d_grad_scale 4-byte
- * aligned (CORR_ERR_INVALID_ARG otherwise). */
+ * aligned (CORR_ERR_INVALID_ARG otherwise).
+ * The input gradient is a GEMM per channel (W' = 2 conj(g) W g times the
+ * samples). With d_in and d_grad_in 16-byte aligned and n_samples > 0 it
+ * runs on the tensor cores in tf32 with
+ * every operand split into a tf32 value and a tf32 remainder (three
+ * products, FP32 accumulation: about FP32 accuracy); otherwise, or with the
+ * environment variable CORR_IG_PATH=cuda_core, as an FP32 GEMM on the CUDA
+ * cores. */
 corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *d_gain,
                                  const void *d_vis_model, const void *d_raw_vis,
                                  void *d_grad_gain, void *d_grad_in, float *d_loss,

@@ -82,6 +82,7 @@ struct corr_plan {
     // gain calibration
     float2 *d_R = nullptr;     // recomputed raw visibilities
     float2 *d_W = nullptr;     // W' per channel
+    float *d_At = nullptr;     // W' as the tensor-core input gradient's A' tiles
     float *d_partial = nullptr;
 };
 
@@ -133,6 +134,33 @@ corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, in
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return CORR_ERR_CUDA;
+    }
+    return CORR_OK;
+}
+
+// The samples for the tensor-core input gradient: the same 4-D view as
+// the FP32 correlator's map, boxes of 4 floats x 8 stations x 256 times x 1
+// unit, landing as 256 linear rows of 128 bytes (one time, 8 stations of
+// both pols). No swizzle mode: with one, each 16-byte inner row of the box
+// would take a 128-byte span of shared memory; the kernel swizzles the rows
+// itself.
+corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long long units)
+{
+    auto fn = encode_fn();
+    if (!fn) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled unavailable");
+        return CORR_ERR_CUDA;
+    }
+    cuuint64_t dims[4] = {4, (cuuint64_t)S, (cuuint64_t)T, (cuuint64_t)units};
+    cuuint64_t strides[3] = {(cuuint64_t)T * 16, 16, (cuuint64_t)S * T * 16};
+    cuuint32_t box[4] = {4, 8, 256, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(d_in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled (input gradient) failed (%d)", (int)r);
         return CORR_ERR_CUDA;
     }
     return CORR_OK;
@@ -1013,6 +1041,11 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             const long long S = d.n_stations, N = 2 * S;
             if ((st = cuda_status(cudaMalloc(&h->d_R, (size_t)(units * n_baselines(S) * 4 * 8)))) != CORR_OK) break;
             if ((st = cuda_status(cudaMalloc(&h->d_W, (size_t)(units * N * N * 8)))) != CORR_OK) break;
+            // the tensor-core input gradient's tiles; their padding (rows or
+            // columns past 4S) is never written: zeroed once
+            const size_t tb = ig_tile_bytes((int)S, units);
+            if ((st = cuda_status(cudaMalloc(&h->d_At, tb))) != CORR_OK) break;
+            if ((st = cuda_status(cudaMemset(h->d_At, 0, tb))) != CORR_OK) break;
             if ((st = cuda_status(cudaMalloc(&h->d_partial, (size_t)units * sizeof(float)))) != CORR_OK) break;
         }
     } while (0);
@@ -1289,10 +1322,36 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     }
     const float2 *g = static_cast<const float2 *>(d_gain);
     const float2 *M = static_cast<const float2 *>(d_vis_model);
+    // The input gradient on the tensor cores (tf32 split, FP32 accuracy)
+    // when the samples and the gradient are 16-byte aligned (TMA loads,
+    // 16-byte stores); otherwise, or with CORR_IG_PATH=cuda_core, the FP32
+    // CUDA-core GEMM.
+    const char *ig = std::getenv("CORR_IG_PATH");
+    const bool tc = d_grad_in && h->d.n_samples > 0 && aligned16(d_in) &&
+                    aligned16(d_grad_in) && !(ig && std::strcmp(ig, "cuda_core") == 0);
+    CUtensorMap xmap{};
+    if (tc) {
+        corr_status_t e = encode_ig_map(&xmap, d_in, S, h->d.n_samples, units);
+        if (e != CORR_OK) return e;
+    }
     corr_status_t e = cuda_status(gain_grad_launch(R, g, M, d_grad_scale, static_cast<float2 *>(d_grad_gain),
-                                                   d_grad_in ? h->d_W : nullptr, S, units, st));
+                                                   tc ? static_cast<void *>(h->d_At) : (d_grad_in ? h->d_W : nullptr),
+                                                   S, units, st, tc ? 1 : 0));
     if (e != CORR_OK) return e;
-    if (d_grad_in) {
+    if (d_grad_in && tc) {
+        IgParams ip{};
+        ip.at = h->d_At;
+        ip.gx = static_cast<float2 *>(d_grad_in);
+        ip.S = S;
+        ip.T = h->d.n_samples;
+        ip.units = units;
+        ip.m_tiles = ig_m_tiles(S);
+        ip.k_blocks = ig_k_blocks(S);
+        ip.err = h->d_err;
+        ip.wait_ns = h->wait_ns;
+        e = cuda_status(input_grad_tc_launch(&xmap, ip, st));
+        if (e != CORR_OK) return e;
+    } else if (d_grad_in) {
         e = cuda_status(input_grad_launch(static_cast<const float2 *>(d_in), h->d_W,
                                           static_cast<float2 *>(d_grad_in), S, h->d.n_samples, units, st));
         if (e != CORR_OK) return e;
@@ -1413,6 +1472,7 @@ corr_status_t corr_destroy(corr_handle_t h)
     if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     cudaFree(h->d_R);
     cudaFree(h->d_W);
+    cudaFree(h->d_At);
     cudaFree(h->d_partial);
     delete h;
     return CORR_OK;

@@ -83,13 +83,39 @@ __global__ void sum_partials_kernel(const float *partial, int n, float *loss)
     if (threadIdx.x == 0) *loss = red[0];
 }
 
+// tf32 split of an FP32 value (corr_gain_tc.cu): hi = the value rounded to
+// tf32, lo = value - hi (exact in FP32) rounded to tf32.
+
+// Writes W'cb = v into the tensor-core input gradient's A' tiles: rows 2c
+// (re) and 2c+1 (im) of M', columns 2b (x re) and 2b+1 (x im) of K', each
+// value as hi and lo in the 128-byte swizzled K-major layout (row r at r x
+// 128 B, 16-byte chunk q at (q ^ (r % 8)) x 16 B).
+__device__ __forceinline__ void store_w_tiles(float *at, int unit, int S, int c, int b, float2 v)
+{
+    const int mt = (2 * c) / 128, r = (2 * c) % 128, kb = (2 * b) / 32, kk = (2 * b) % 32;
+    const size_t tile = (((size_t)unit * ig_m_tiles(S) + mt) * ig_k_blocks(S) + kb) * 2;   // hi; lo = tile + 1
+    const int q = kk >> 2;
+    const float vals[2][2] = {{v.x, -v.y}, {v.y, v.x}};   // rows r (re) and r + 1 (im)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int rr = r + h;
+        const size_t off = (size_t)rr * 32 + (size_t)((q ^ (rr & 7)) << 2) + (kk & 3);
+        const float a0 = vals[h][0], a1 = vals[h][1];
+        const float h0 = tf32_round(a0), h1 = tf32_round(a1);
+        *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(h0, h1);
+        *reinterpret_cast<float2 *>(at + (tile + 1) * 4096 + off) = make_float2(tf32_round(a0 - h0), tf32_round(a1 - h1));
+    }
+}
+
 // One CTA per (unit, row c = (s, p)), its threads over b: the residuals of
 // row c give both sums of dL/d conj(g_c) (reduced over b in a fixed order)
 // and, when W is given, the row W'[unit][c][:] = 2 scale conj(g_c) W_cb g_b of
-// the input gradient.
+// the input gradient (TILES: written as the tensor-core path's A' tiles).
+template <bool TILES>
 __global__ void __launch_bounds__(256) gain_grad_w_kernel(const float2 *R, const float2 *g, const float2 *M,
-                                                          const float *scale, float2 *grad, float2 *W, int S)
+                                                          const float *scale, float2 *grad, void *Wv, int S)
 {
+    float2 *W = TILES ? nullptr : static_cast<float2 *>(Wv);
     const int N = 2 * S;
     const int c = (int)(blockIdx.x % (unsigned)N), unit = (int)(blockIdx.x / (unsigned)N);
     const int sc = c >> 1, pc = c & 1;
@@ -122,7 +148,10 @@ __global__ void __launch_bounds__(256) gain_grad_w_kernel(const float2 *R, const
             w.x += e.x;
             w.y -= e.y;
         }
-        if (W) {
+        if (TILES) {
+            const float2 v = cmul(cmul(gc, w), gb);
+            store_w_tiles(static_cast<float *>(Wv), unit, S, c, b, make_float2(s * v.x, s * v.y));
+        } else if (W) {
             const float2 v = cmul(cmul(gc, w), gb);
             W[((long long)unit * N + c) * N + b] = make_float2(s * v.x, s * v.y);
         }
@@ -252,14 +281,16 @@ cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, 
 
 cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
                              const float *scale, float2 *grad_g, void *W, int S, int units,
-                             cudaStream_t s)
+                             cudaStream_t s, int tiles)
 {
     const int N = 2 * S;
     // threads: a power of two (the reduction halves), up to 256, about N
     int threads = 32;
     while (threads < N && threads < 256) threads <<= 1;
-    gain_grad_w_kernel<<<(unsigned)((long long)N * units), threads, 0, s>>>(
-        R, g, M, scale, grad_g, static_cast<float2 *>(W), S);
+    if (tiles && W)
+        gain_grad_w_kernel<true><<<(unsigned)((long long)N * units), threads, 0, s>>>(R, g, M, scale, grad_g, W, S);
+    else
+        gain_grad_w_kernel<false><<<(unsigned)((long long)N * units), threads, 0, s>>>(R, g, M, scale, grad_g, W, S);
     return cudaGetLastError();
 }
 
@@ -273,8 +304,13 @@ cudaError_t input_grad_launch(const float2 *x, const float2 *W, float2 *grad_x, 
         cudaError_t e = cudaFuncSetAttribute(input_grad_gemm_kernel<CORR_IG_TM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((T + 63) / 64, (unsigned)((N + BM - 1) / BM), units);
-        input_grad_gemm_kernel<CORR_IG_TM><<<grid, 256, smem, s>>>(W, x, grad_x, S, T);
+        // at most 65535 units per launch (the grid's z dimension)
+        for (long long u0 = 0; u0 < units; u0 += 65535) {
+            const unsigned n = (unsigned)std::min<long long>(65535, units - u0);
+            dim3 grid((T + 63) / 64, (unsigned)((N + BM - 1) / BM), n);
+            input_grad_gemm_kernel<CORR_IG_TM><<<grid, 256, smem, s>>>(W + u0 * N * N, x + u0 * S * T * 2,
+                                                                        grad_x + u0 * S * T * 2, S, T);
+        }
     }
     return cudaGetLastError();
 }

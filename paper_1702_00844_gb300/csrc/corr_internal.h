@@ -41,9 +41,29 @@ cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, 
                              float *partial, float *loss, int S, int units, cudaStream_t s);
 // dL/d conj(g); with W (units x 2S x 2S complex64) also the matrix W' of the
 // input gradient, from the same residuals.
+// Input gradient on the tensor cores (corr_gain_tc.cu): A' tiles written
+// by gain_grad_launch in tile mode, samples through a TMA map of boxes of
+// 4 floats x 8 stations x 256 times (128-byte swizzle).
+struct IgParams {
+    const float *at;          // A' tiles [unit][m tile][k block][hi, lo][128 x 32 floats]
+    float2 *gx;               // [unit][S][T][2] complex
+    int S, T, units, m_tiles, k_blocks;
+    int unit0;                // first unit of this launch (blockIdx.z counts from it)
+    int *err;
+    unsigned long long wait_ns;
+};
+// Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
+__host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
+__host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }
+inline size_t ig_tile_bytes(int S, long long units)
+{
+    return (size_t)units * ig_m_tiles(S) * ig_k_blocks(S) * 2 * 16384;
+}
+cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s);
+// tiles = 1: W is the A' tile buffer (zeroed once, its padding never written)
 cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
                              const float *scale, float2 *grad_g, void *W, int S, int units,
-                             cudaStream_t s);
+                             cudaStream_t s, int tiles = 0);
 // dL/d conj(x) = W' x per channel (W' from gain_grad_launch).
 cudaError_t input_grad_launch(const float2 *x, const float2 *W, float2 *grad_x, int S, int T, int units,
                               cudaStream_t s);

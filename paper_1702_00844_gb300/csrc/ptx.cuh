@@ -176,6 +176,16 @@ __device__ __forceinline__ void tma_load_4d(void *smem_dst, const void *tmap, ui
         : "memory");
 }
 
+// Bulk copy of `bytes` contiguous bytes global -> shared (both 16-byte
+// aligned, bytes a multiple of 16), completing as transaction bytes on *bar.
+__device__ __forceinline__ void bulk_load_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 16-byte asynchronous copy global -> shared; bytes beyond src_bytes (0..16)
 // are zero-filled. Pending copies are not waited for by barriers; the
 // issuing thread waits for its own groups with cp_async_wait.
@@ -303,6 +313,19 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uin
         : "memory");
 }
 
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::tf32 (32-bit operands of
+// which the tensor core uses the tf32 bits), FP32 accumulation, one CTA.
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrives once on *bar when all prior tcgen05 async operations of this thread
 // have completed.
 __device__ __forceinline__ void tc_commit(uint64_t *bar)
@@ -421,6 +444,23 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N, bool neg_a)
 {
     return (1u << 4) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// v rounded to the nearest tf32 value (ties away from zero), returned with
+// the 13 low mantissa bits cleared, so that it is exactly what the tensor
+// core's kind::tf32 reads.
+__device__ __forceinline__ float tf32_round(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r & 0xFFFFE000u);
+}
+
+// Instruction descriptor of kind::tf32: A and B tf32 (format 2 in bits 7-9
+// and 10-12), f32 accumulator, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 } // namespace corr

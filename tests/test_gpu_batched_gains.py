@@ -220,6 +220,106 @@ def test_differentiation_workload_full_size():
         assert np.abs(gx - xref).max() < 1e-4 * np.abs(xref).max()
 
 
+def _input_grad(plan, xd, gd, Md, R, grad_x):
+    """corr_gain_backward into a caller-given grad_x buffer."""
+    import ctypes
+    grad_g = torch.empty_like(gd)
+    st = plan.L.corr_gain_backward(plan.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(gd.data_ptr()),
+                                   ctypes.c_void_p(Md.data_ptr()), ctypes.c_void_p(R.data_ptr()),
+                                   ctypes.c_void_p(grad_g.data_ptr()), ctypes.c_void_p(grad_x.data_ptr()),
+                                   None, None, None)
+    assert st == 0, plan.L.corr_last_error_message()
+    torch.cuda.synchronize()
+    plan.check_error()
+    return grad_x.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("S,C,T", [(8, 2, 64), (37, 2, 300), (70, 3, 700)])
+def test_input_gradient_tensor_and_cuda_core_paths_vs_oracle(S, C, T, monkeypatch):
+    """dL/dx on the tensor cores (the default for 16-byte aligned buffers:
+    tf32 with each operand split into value and remainder) and on the CUDA
+    cores (CORR_IG_PATH=cuda_core), both against the oracle. The shapes span
+    one to three 128-row tiles of 4S, a K block that 4S fills only in part
+    (S = 37, 70) and a last time tile of fewer than 256 samples. 2e-5 of the
+    largest element is FP32-class accuracy: one unsplit tf32 product would
+    miss it by about two orders of magnitude."""
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    x, gains, M = gain_case(S, C, T, seed=90 + S)
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    R = plan.correlate(xd)
+    Rref = oracle.correlate(x)
+    xref = oracle.input_grad(x, Rref, gains, M)
+    scale = np.abs(xref).max()
+    got = {}
+    for path in ("tensor", "cuda_core"):
+        if path == "cuda_core":
+            monkeypatch.setenv("CORR_IG_PATH", "cuda_core")
+        else:
+            monkeypatch.delenv("CORR_IG_PATH", raising=False)
+        got[path] = _input_grad(plan, xd, gd, Md, R, torch.full_like(xd, float("nan")))
+        assert np.isfinite(got[path]).all(), path
+        assert np.abs(got[path] - xref).max() < 2e-5 * scale, path
+    # the two paths round differently: equal bits would mean one did not run
+    assert not np.array_equal(got["tensor"], got["cuda_core"])
+
+
+def test_input_gradient_unaligned_buffers_take_the_cuda_core_path():
+    """grad_x (or x) 8 bytes past a 16-byte boundary: the tensor path's TMA
+    loads and 16-byte stores do not apply, the CUDA-core path runs and gives
+    the same bits as CORR_IG_PATH=cuda_core on aligned buffers."""
+    import os
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    S, C, T = 20, 2, 96
+    x, gains, M = gain_case(S, C, T, seed=95)
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    R = plan.correlate(xd)
+    xref = oracle.input_grad(x, oracle.correlate(x), gains, M)
+    flat = torch.full((xd.numel() + 1,), float("nan"), dtype=torch.complex64, device="cuda")
+    out = flat[1:].view(xd.shape)
+    assert out.data_ptr() % 16 == 8
+    unaligned = _input_grad(plan, xd, gd, Md, R, out)
+    assert np.abs(unaligned - xref).max() < 2e-5 * np.abs(xref).max()
+    xflat = torch.empty((xd.numel() + 1,), dtype=torch.complex64, device="cuda")
+    x_off = xflat[1:].view(xd.shape)
+    x_off.copy_(xd)
+    unaligned_x = _input_grad(plan, x_off, gd, Md, R, torch.full_like(xd, float("nan")))
+    os.environ["CORR_IG_PATH"] = "cuda_core"
+    try:
+        core = _input_grad(plan, xd, gd, Md, R, torch.full_like(xd, float("nan")))
+    finally:
+        del os.environ["CORR_IG_PATH"]
+    assert np.array_equal(unaligned, core)
+    assert np.array_equal(unaligned_x, core)
+
+
+def test_input_gradient_beyond_65535_units(monkeypatch):
+    """65541 channels of 2 stations: more units than a grid's z dimension
+    holds, so both paths launch in chunks of 65535 units (sampled channels
+    against the oracle, on both sides of the chunk boundary)."""
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    S, C, T = 2, 65541, 16
+    g = synth.rng(96)
+    x = synth.complex_normal(g, (C, S, T, 2))
+    gains = (1 + synth.complex_normal(g, (C, S, 2), sigma=0.1)).astype(np.complex64)
+    M = synth.complex_normal(g, (C, S * (S + 1) // 2, 2, 2)).astype(np.complex64)
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = _dev(x), _dev(gains), _dev(M)
+    R = plan.correlate(xd)
+    for path in ("tensor", "cuda_core"):
+        if path == "cuda_core":
+            monkeypatch.setenv("CORR_IG_PATH", "cuda_core")
+        else:
+            monkeypatch.delenv("CORR_IG_PATH", raising=False)
+        gx = _input_grad(plan, xd, gd, Md, R, torch.full_like(xd, float("nan")))
+        assert np.isfinite(gx).all(), path
+        for c in (0, 65534, 65535, C - 1):
+            Rref = oracle.correlate(x[c][None])
+            xref = oracle.input_grad(x[c][None], Rref, gains[c][None], M[c][None])
+            assert np.abs(gx[c][None] - xref).max() < 2e-5 * np.abs(xref).max(), (path, c)
+
+
 def test_ragged_int8_batch_with_extreme_subarray_takes_redo_path(monkeypatch):
     """One sub-array of all +-127 samples (station power above 2^24) in a
     batch with T > 512: its tiles fail the power check and are recomputed in
