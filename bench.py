@@ -53,11 +53,14 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["precision", "precision-f16", "production"],
+    ap.add_argument("--workload", choices=["precision", "precision-f16", "production", "ragged"],
                     default="precision",
                     help="precision: int8 tensor path at 256 stations (the headline); "
                          "precision-f16: the same samples on the f16 tensor path; "
-                         "production: the 64-station FP32 workload on the FP32 path")
+                         "production: the 64-station FP32 workload on the FP32 path; "
+                         "ragged: the 32-sub-array f16 batch alone")
+    ap.add_argument("--ragged-scale", type=float, default=1.0,
+                    help="channels of each ragged sub-array scaled by this factor")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/FP32/batch/adjoint side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -290,6 +293,75 @@ def time_launches(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps  # ms
 
 
+def ragged_shapes(scale=1.0):
+    """The ragged-batch workload's 32 (stations, channels, samples) shapes,
+    channels scaled by ``scale`` (at least one per sub-array)."""
+    import synth
+    return [(S, max(1, int(round(C * scale))), T) for S, C, T in synth.batching_shapes()]
+
+
+def ragged_batch(torch, scale=1.0, steps=5, warmup=2):
+    """The ragged batch (32 sub-arrays of 16-576 stations and 256-4096
+    samples, complex f16) correlated by one corr_correlate_batched call,
+    captured in a CUDA graph and replayed: ms per replay, TOPS, the clocks
+    during the replays and the tile configuration the batch tuner chose.
+    A replay of the full batch lasts about 45 ms, so the replays are a
+    sustained load: the fraction is also given against the sustained bf16
+    peak."""
+    import synth
+    from paper_1702_00844_gb300 import Plan
+    shapes = ragged_shapes(scale)
+    xs, outs = [], []
+    for k, (S, C, T) in enumerate(shapes):
+        xs.append(synth.batching_subarray_device(S, C, T, k, "cuda"))
+        outs.append(torch.empty((C, S * (S + 1) // 2, 2, 2), dtype=torch.complex64, device="cuda"))
+    pb = Plan(1, 1, 1, dtype="cf16", path="tensor")
+    pairs = list(zip(xs, outs))
+    pb.correlate_batched(pairs, shapes)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pb.correlate_batched(pairs, shapes, stream=s)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_launches(g.replay, steps, warmup, torch.cuda.current_stream())
+    opsb = sum(ops_of(S, T, C) for S, C, T in shapes)
+    peaks, _ = measured_peaks()
+    res = {"ms": ms, "TOPS": opsb / ms / 1e9, "ops": opsb, "steps": steps, "clocks": clk.summary(),
+           "frac_sustained": opsb / ms / 1e9 / float(peaks.get("bf16_tflops_sustained", 1700.0)),
+           "input_GB": sum(x.numel() * 2 for x in xs) / 1e9,
+           "channel_scale": scale,
+           "variant": pb.batch_tile_variant(),
+           "tuned": [["/".join(map(str, c)), round(t, 3)] for c, t in pb.tune_results(batch=True)]}
+    pb.check_error()
+    del xs, outs, pairs, g, pb
+    return res
+
+
+def run_ragged(args):
+    """--workload ragged: the ragged batch alone on one GPU (rank 0), one
+    JSON line; --ragged-scale shrinks its channels for profiler captures."""
+    import torch
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    r = ragged_batch(torch, args.ragged_scale, max(1, args.steps), max(3, args.warmup))
+    line = {"metric": METRIC, "value": r["TOPS"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic (seeded device Philox)",
+            "config": {"workload": "ragged batch: 32 sub-arrays, 16-576 stations, 256-4096 samples, "
+                                   f"channels x {args.ragged_scale:g}, complex f16, one batched call "
+                                   "replayed as a CUDA graph",
+                       "l2": f"inputs {r['input_GB']:.2f} GB"},
+            "clocks": r["clocks"],
+            "roofline": {"bound": "tensor", "achieved": r["TOPS"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": r["TOPS"] / peak, "traffic": None,
+                         "peak_source": f"{peak_src} bf16 dense burst"},
+            "batch": r}
+    print(json.dumps(line), flush=True)
+
+
 def secondary(x8, torch):
     """Side measurements on one GPU: FP16 and FP32 paths on the same samples,
     the production FP32 workload, the ragged batch and the gain adjoint."""
@@ -303,6 +375,14 @@ def secondary(x8, torch):
     o16 = p16.empty_out()
     ms = time_launches(lambda: p16.correlate(x16, o16), 10, 3, st)
     res["tensor_fp16_precision"] = {"ms": ms, "TOPS": ops3 / ms / 1e9}
+    # the same for about a second of back-to-back steps: a sustained load
+    # like the ragged batch's replays (the power limit lowers the clocks)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_launches(lambda: p16.correlate(x16, o16), 2000, 3, st)
+    peaks, _ = measured_peaks()
+    res["tensor_fp16_precision_sustained"] = {
+        "ms": ms, "TOPS": ops3 / ms / 1e9, "steps": 2000, "clocks": clk.summary(),
+        "frac_sustained": ops3 / ms / 1e9 / float(peaks.get("bf16_tflops_sustained", 1700.0))}
     del o16, x16, p16
     xc = torch.view_as_complex(x8.to(torch.float32).contiguous())
     p32 = Plan(S3, C3, T3, dtype="cf32", path="fp32")
@@ -323,28 +403,7 @@ def secondary(x8, torch):
     del x2, o2, p2
     torch.cuda.empty_cache()
     # ragged batch: 32 sub-arrays, one persistent launch (graph replay)
-    shapes = synth.batching_shapes()
-    xs, outs = [], []
-    for k, (S, C, T) in enumerate(shapes):
-        xs.append(synth.batching_subarray_device(S, C, T, k, "cuda"))
-        outs.append(torch.empty((C, S * (S + 1) // 2, 2, 2), dtype=torch.complex64, device="cuda"))
-    pb = Plan(1, 1, 1, dtype="cf16", path="tensor")
-    pairs = list(zip(xs, outs))
-    pb.correlate_batched(pairs, shapes)
-    torch.cuda.synchronize()
-    s = torch.cuda.Stream()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        pb.correlate_batched(pairs, shapes, stream=s)
-    ms = time_launches(g.replay, 5, 2, torch.cuda.current_stream())
-    opsb = sum(ops_of(S, T, C) for S, C, T in shapes)
-    res["tensor_fp16_ragged_batch"] = {"ms": ms, "TOPS": opsb / ms / 1e9, "ops": opsb,
-                                       "input_GB": sum(x.numel() * 2 for x in xs) / 1e9,
-                                       "variant": pb.batch_tile_variant(),
-                                       "tuned": [["/".join(map(str, c)), round(t, 3)]
-                                                 for c, t in pb.tune_results(batch=True)]}
-    pb.check_error()
-    del xs, outs, pairs, g, pb
+    res["tensor_fp16_ragged_batch"] = ragged_batch(torch, steps=20)
     torch.cuda.empty_cache()
     # gain adjoint: 64 stations, 64 channels, 1024 samples
     d = synth.differentiation()
@@ -581,6 +640,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ragged":
+        run_ragged(args)
     else:
         run_ours(args)
 

@@ -139,12 +139,11 @@ corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, in
     return CORR_OK;
 }
 
-// The samples for the tensor-core input gradient: the same 4-D view as
-// the FP32 correlator's map, boxes of 4 floats x 8 stations x 256 times x 1
-// unit, landing as 256 linear rows of 128 bytes (one time, 8 stations of
-// both pols). No swizzle mode: with one, each 16-byte inner row of the box
-// would take a 128-byte span of shared memory; the kernel swizzles the rows
-// itself.
+// The samples for the tensor-core input gradient as 8-byte elements (one
+// complex float each, copied bit for bit): dims (2T per station, stations,
+// units, 1), boxes of 2 CORR_IG_N elements x 8 stations: one contiguous run
+// of CORR_IG_N x 16 bytes per station, landing station-major. No swizzle
+// mode; the kernel transposes and swizzles.
 corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long long units)
 {
     auto fn = encode_fn();
@@ -152,11 +151,11 @@ corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long
         snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled unavailable");
         return CORR_ERR_CUDA;
     }
-    cuuint64_t dims[4] = {4, (cuuint64_t)S, (cuuint64_t)T, (cuuint64_t)units};
-    cuuint64_t strides[3] = {(cuuint64_t)T * 16, 16, (cuuint64_t)S * T * 16};
-    cuuint32_t box[4] = {4, 8, 256, 1};
+    cuuint64_t dims[4] = {2 * (cuuint64_t)T, (cuuint64_t)S, (cuuint64_t)units, 1};
+    cuuint64_t strides[3] = {(cuuint64_t)T * 16, (cuuint64_t)S * T * 16, (cuuint64_t)units * S * T * 16};
+    cuuint32_t box[4] = {2 * CORR_IG_N, 8, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(d_in), dims, strides, box, estr,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(d_in), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {

@@ -17,21 +17,25 @@
 // accumulated in FP32 (the dropped A_lo B_lo and lo's rounding are about
 // 2^-22 of each product).
 //
-// One CTA per (channel, 128-row tile of M', 256-time tile of N). Per K-block
-// of 32 reduction values (8 stations x 2 pols x re/im):
+// Tiles of (channel, 128-row tile of M', IG_N-time tile of N), spread over
+// one persistent CTA per SM. Per K-block of 32 reduction values (8 stations
+// x 2 pols x re/im), through a ring of operand stages that runs on across
+// the CTA's tiles:
 //   - one thread issues the loads: A_hi and A_lo as 16 KB bulk copies of
 //     tiles that the gain-gradient kernel wrote already split and swizzled,
-//     and the samples with one TMA box of 4 floats x 8 stations x 256 times,
-//     which lands as 256 K-major rows (one time each) of 128 bytes (without
-//     a swizzle mode: with one, TMA would give each 16-byte inner row of the
-//     box a 128-byte span of its own);
-//   - 128 threads split the samples into hi and lo and move each 16-byte
-//     chunk j of row t to chunk j ^ (t mod 8), the 128-byte swizzled layout
-//     the MMA reads (hi in place, lo in its own tile);
-//   - one thread issues 4 K-steps x 3 MMAs (M = 128, N = 256, K = 8).
-// The same 128 threads then store the accumulator: TMEM -> registers ->
+//     and the samples with one TMA box of IG_N times (16 bytes each, 2 IG_N
+//     8-byte elements: one contiguous run) x 8 stations, landing
+//     station-major in the lo tile;
+//   - 128 threads split the samples into hi and lo and transpose them into
+//     K-major rows (one time each) of 8 stations x 16 bytes, the chunk of
+//     station j in row t at 16-byte position j ^ (t mod 8): the 128-byte
+//     swizzled layout the MMA reads;
+//   - one thread issues 4 K-steps x 3 MMAs (M = 128, N = IG_N, K = 8) into
+//     one of two TMEM accumulators, alternating per tile;
+// and four more warps store each finished accumulator (TMEM -> registers ->
 // a per-warp transpose in shared memory -> 16-byte stores of (XX, YY)
-// complex pairs of one station and time.
+// complex pairs of one station and time) while the next tile's MMAs run in
+// the other one.
 // Every wait is bounded (mbar_wait_bounded).
 #include <cuda.h>
 
@@ -42,26 +46,48 @@ namespace corr {
 
 namespace {
 
-constexpr int IG_THREADS = 192;          // warp 0 loads, warps 1-4 split and store, warp 5 MMAs
-constexpr int IG_M = 128, IG_N = 256;    // tile: rows of M' x times
-constexpr int IG_STAGES = 2;
+// warp 0 loads, warps 1-4 split, warps 5-8 store (TMEM lane quarters 1, 2,
+// 3, 0), warp 9 allocates TMEM and issues the MMAs
+constexpr int IG_THREADS = 320;
+constexpr int IG_M = 128, IG_N = CORR_IG_N;    // tile: rows of M' x times
+constexpr int IG_STAGES = CORR_IG_STAGES;
 constexpr uint32_t IG_A_BYTES = IG_M * 128;      // 16 KB: 128 rows x 32 tf32
-constexpr uint32_t IG_B_BYTES = IG_N * 128;      // 32 KB: 256 rows x 32 tf32
+constexpr uint32_t IG_B_BYTES = IG_N * 128;      // IG_N rows x 32 tf32
 constexpr uint32_t IG_STAGE_BYTES = 2 * IG_A_BYTES + 2 * IG_B_BYTES;   // A hi, A lo, B hi, B lo
 constexpr uint32_t IG_EPI_BYTES = 4 * 32 * 17 * 4;                       // per-warp transpose
-constexpr uint32_t IG_TMEM_COLS = 256;
+constexpr uint32_t IG_TMEM_COLS = 2 * IG_N;      // two accumulators
+static_assert(IG_N == 64 || IG_N == 128, "input-gradient tile width (a TMA box row holds at most 256 elements)");
 
 struct IgBars {
     uint64_t raw[IG_STAGES];     // loads landed (transaction bytes)
+    uint64_t rd[IG_STAGES];      // raw samples read into registers (128 arrivals)
     uint64_t full[IG_STAGES];    // samples split (128 arrivals)
     uint64_t empty[IG_STAGES];   // MMAs of the stage done (commit)
-    uint64_t acc_full;           // all MMAs done (commit)
+    uint64_t acc_full[2];        // a tile's MMAs done (commit)
+    uint64_t acc_empty[2];       // a tile's accumulator read out (4 warps)
+    uint64_t done;               // every MMA issued has completed (commit)
     uint32_t tmem_base;
     int abort_flag;
 };
 
 constexpr size_t ig_smem_bytes() { return IG_STAGES * IG_STAGE_BYTES + IG_EPI_BYTES + sizeof(IgBars) + 1024; }
 static_assert(ig_smem_bytes() <= 227 * 1024, "input-gradient tiles must fit in shared memory");
+
+struct IgTile {
+    int nt, mt, unit;
+};
+
+// Tile `tile` of the flattened (unit, row tile, time tile) space, time
+// tiles fastest (consecutive tiles share their A' tiles).
+__device__ __forceinline__ IgTile ig_tile(long long tile, int n_times, const IgParams &p)
+{
+    IgTile r;
+    r.nt = (int)(tile % n_times);
+    const long long rest = tile / n_times;
+    r.mt = (int)(rest % p.m_tiles);
+    r.unit = (int)(rest / p.m_tiles);
+    return r;
+}
 
 __global__ void __launch_bounds__(IG_THREADS, 1)
     input_grad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const IgParams p)
@@ -74,25 +100,29 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
     volatile int *abort_flag = &bars->abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = blockIdx.x, mt = blockIdx.y, unit = p.unit0 + (int)blockIdx.z;
-    const int t0 = nt * IG_N;
     const int KB = p.k_blocks;
-    // A' tiles of this (unit, row tile): [k block][hi, lo][128 rows x 128 B]
-    const uint8_t *a_tiles =
-        reinterpret_cast<const uint8_t *>(p.at) + ((size_t)unit * p.m_tiles + mt) * (size_t)KB * 2 * IG_A_BYTES;
+    const int n_times = (p.T + IG_N - 1) / IG_N;
+    const long long n_tiles = (long long)n_times * p.m_tiles * p.units;
+    // this CTA's tiles: blockIdx.x, + gridDim.x, ...
+    const int my_tiles = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
     if (tid == 0) {
         prefetch_tmap(&xmap);
         for (int s = 0; s < IG_STAGES; ++s) {
             mbar_init(&bars->raw[s], 1);
+            mbar_init(&bars->rd[s], 128);
             mbar_init(&bars->full[s], 128);
             mbar_init(&bars->empty[s], 1);
         }
-        mbar_init(&bars->acc_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], 4);
+        }
+        mbar_init(&bars->done, 1);
         bars->abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 5) {
+    if (warp == 9) {
         tmem_alloc(&bars->tmem_base, IG_TMEM_COLS);
         tmem_relinquish();
     }
@@ -108,93 +138,127 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
     if (warp == 0) {
         // ----------------------------------------------------------- loads
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < KB; ++kb) {
-                const int s = kb % IG_STAGES;
-                if (kb >= IG_STAGES &&
-                    !mbar_wait_bounded(&bars->empty[s], ((kb / IG_STAGES) - 1) & 1, abort_flag, p.err, p.wait_ns))
-                    break;
-                mbar_arrive_expect_tx(&bars->raw[s], 2 * IG_A_BYTES + IG_B_BYTES);
-                bulk_load_g2s(a_hi(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES, IG_A_BYTES, &bars->raw[s]);
-                bulk_load_g2s(a_lo(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES + IG_A_BYTES, IG_A_BYTES, &bars->raw[s]);
-                // the 8 stations of this K block, 256 times from t0 (zero outside)
-                tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES, &xmap, &bars->raw[s], 0, kb * 8, t0,
-                            unit);
-                ++issued;
+            long long g = 0;   // K blocks issued so far (over all tiles)
+            bool ok = true;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const IgTile tl = ig_tile(blockIdx.x + (long long)i * gridDim.x, n_times, p);
+                // A' tiles of this (unit, row tile): [k block][hi, lo][128 rows x 128 B]
+                const uint8_t *a_tiles = reinterpret_cast<const uint8_t *>(p.at) +
+                                         ((size_t)tl.unit * p.m_tiles + tl.mt) * (size_t)KB * 2 * IG_A_BYTES;
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int s = (int)(g % IG_STAGES);
+                    if (g >= IG_STAGES && !mbar_wait_bounded(&bars->empty[s], (uint32_t)((g / IG_STAGES) - 1) & 1,
+                                                             abort_flag, p.err, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&bars->raw[s], 2 * IG_A_BYTES + IG_B_BYTES);
+                    bulk_load_g2s(a_hi(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES, IG_A_BYTES, &bars->raw[s]);
+                    bulk_load_g2s(a_lo(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES + IG_A_BYTES, IG_A_BYTES,
+                                  &bars->raw[s]);
+                    // the 8 stations of this K block, IG_N times from the
+                    // tile's first (zero outside), into the lo tile
+                    tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES + IG_B_BYTES, &xmap,
+                                &bars->raw[s], 2 * tl.nt * IG_N, kb * 8, tl.unit, 0);
+                }
             }
             // on a give-up, let the copies in flight land before the CTA (and
             // its shared memory) goes away; fixed 2 s bound per stage
             if (*abort_flag) {
                 int dummy = 0;
-                for (int kb = issued > IG_STAGES ? issued - IG_STAGES : 0; kb < issued; ++kb)
-                    mbar_wait_bounded(&bars->raw[kb % IG_STAGES], (kb / IG_STAGES) & 1, &dummy, p.err,
+                for (long long q = g > IG_STAGES ? g - IG_STAGES : 0; q < g; ++q)
+                    mbar_wait_bounded(&bars->raw[q % IG_STAGES], (uint32_t)(q / IG_STAGES) & 1, &dummy, p.err,
                                       2000000000ull);
             }
         }
         __syncwarp();
     } else if (warp <= 4) {
-        // ---------------------------------------- split, then the epilogue
+        // ------------------------------------------------------------ split
         const int pt = tid - 32;   // 0 .. 127
+        long long g = 0;
         bool ok = true;
-        for (int kb = 0; kb < KB && ok; ++kb) {
-            const int s = kb % IG_STAGES;
-            if (!mbar_wait_bounded(&bars->raw[s], (kb / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
-                ok = false;
-                break;
+        for (int i = 0; i < my_tiles && ok; ++i) {
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = (int)(g % IG_STAGES);
+                if (!mbar_wait_bounded(&bars->raw[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                // chunk i = q * 128 + pt of the raw box (landed in the lo
+                // tile) is (station i / IG_N, time i % IG_N): consecutive
+                // threads read consecutive times of one station. Once all
+                // 128 threads hold their chunks (rd), each writes hi and lo
+                // into row t at 16-byte position (station ^ (t mod 8)).
+                constexpr int CH = IG_N / 16;   // chunks per thread
+                uint4 v[CH];
+#pragma unroll
+                for (int q = 0; q < CH; ++q) v[q] = lds128(b_lo(s) + (uint32_t)((q * 128 + pt) * 16));
+                mbar_arrive(&bars->rd[s]);
+                if (!mbar_wait_bounded(&bars->rd[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const int i = q * 128 + pt, st = i / IG_N, t = i % IG_N;
+                    const float4 f = make_float4(__uint_as_float(v[q].x), __uint_as_float(v[q].y),
+                                                 __uint_as_float(v[q].z), __uint_as_float(v[q].w));
+                    const float4 hf =
+                        make_float4(tf32_round(f.x), tf32_round(f.y), tf32_round(f.z), tf32_round(f.w));
+                    const uint4 h = make_uint4(__float_as_uint(hf.x), __float_as_uint(hf.y), __float_as_uint(hf.z),
+                                               __float_as_uint(hf.w));
+                    const uint4 l = make_uint4(
+                        __float_as_uint(tf32_round(f.x - hf.x)), __float_as_uint(tf32_round(f.y - hf.y)),
+                        __float_as_uint(tf32_round(f.z - hf.z)), __float_as_uint(tf32_round(f.w - hf.w)));
+                    const uint32_t sw = (uint32_t)(t * 128 + ((st ^ (t & 7)) * 16));
+                    sts128(b_hi(s) + sw, h);
+                    sts128(b_lo(s) + sw, l);
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bars->full[s]);
             }
-            // 8 lanes per row: each reads one 16-byte chunk of the linear
-            // row, the warp waits until all its rows are read, then each lane
-            // writes hi and lo to the chunk's swizzled position (a row stays
-            // within one warp, so no other warp touches it)
-            const int wp = pt >> 5, j = lane & 7;
-#pragma unroll 4
-            for (int q = 0; q < IG_N / 16; ++q) {
-                const int t = q * 16 + wp * 4 + (lane >> 3);
-                const uint4 v = lds128(b_hi(s) + (uint32_t)(t * 128 + j * 16));
-                __syncwarp();
-                const float4 f = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
-                                             __uint_as_float(v.w));
-                const float4 hf = make_float4(tf32_round(f.x), tf32_round(f.y), tf32_round(f.z), tf32_round(f.w));
-                const uint4 h = make_uint4(__float_as_uint(hf.x), __float_as_uint(hf.y), __float_as_uint(hf.z),
-                                           __float_as_uint(hf.w));
-                const uint4 l = make_uint4(__float_as_uint(tf32_round(f.x - hf.x)), __float_as_uint(tf32_round(f.y - hf.y)),
-                                           __float_as_uint(tf32_round(f.z - hf.z)), __float_as_uint(tf32_round(f.w - hf.w)));
-                const uint32_t sw = (uint32_t)(t * 128 + ((j ^ (t & 7)) * 16));
-                sts128(b_hi(s) + sw, h);
-                sts128(b_lo(s) + sw, l);
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&bars->full[s]);
         }
-        if (ok && mbar_wait_bounded(&bars->acc_full, 0, abort_flag, p.err, p.wait_ns)) {
+    } else if (warp <= 8) {
+        // --------------------------------------------------------- epilogue
+        // TMEM lanes of this warp: 32 * (warp % 4) ..; lane r of the tile
+        // is row m = 128 mt + r of M': c = m / 2 = (station, pol), and re
+        // (r even) or im. A quad of lanes holds (X re, X im, Y re, Y im) of
+        // one station.
+        const int quarter = warp & 3;
+        float *w = epi + (size_t)quarter * 32 * 17;
+        const int k = lane & 3, quad = lane & ~3;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait_bounded(&bars->acc_full[b], (uint32_t)(i >> 1) & 1, abort_flag, p.err, p.wait_ns))
+                break;
             tc_fence_after();
-            // TMEM lanes of this warp: 32 * (warp % 4) ..; lane r of the tile
-            // is row m = 128 mt + r of M': c = m / 2 = (station, pol), and
-            // re (r even) or im. A quad of lanes holds (X re, X im, Y re, Y im)
-            // of one station.
-            const int quarter = warp & 3;
-            const int r = quarter * 32 + lane;
-            const int station = (IG_M * mt + quarter * 32) / 4 + (lane >> 2);
-            float *w = epi + (size_t)quarter * 32 * 17;
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
-            const int k = lane & 3, quad = lane & ~3;
-            (void)r;
+            const IgTile tl = ig_tile(blockIdx.x + (long long)i * gridDim.x, n_times, p);
+            const int station = (IG_M * tl.mt + quarter * 32) / 4 + (lane >> 2);
+            const int t0 = tl.nt * IG_N;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * IG_N);
             for (int cg = 0; cg < IG_N / 16; ++cg) {
                 uint32_t v[16];
                 tmem_ld_32x32b_x16(taddr + cg * 16, v);
                 tmem_wait_ld();
+                if (cg == IG_N / 16 - 1) {
+                    // the accumulator is read out: the next tile but one may
+                    // start its MMAs in it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bars->acc_empty[b]);
+                }
 #pragma unroll
                 for (int m = 0; m < 16; ++m) w[lane * 17 + m] = __uint_as_float(v[m]);
                 __syncwarp();
                 // lane k of the quad stores times m = k, k + 4, k + 8, k + 12
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int m = k + 4 * i;
+                for (int q = 0; q < 4; ++q) {
+                    const int m = k + 4 * q;
                     const int t = t0 + cg * 16 + m;
                     const float4 o = make_float4(w[(quad + 0) * 17 + m], w[(quad + 1) * 17 + m],
                                                  w[(quad + 2) * 17 + m], w[(quad + 3) * 17 + m]);
                     if (station < p.S && t < p.T)
-                        *reinterpret_cast<float4 *>(p.gx + (((size_t)unit * p.S + station) * p.T + t) * 2) = o;
+                        *reinterpret_cast<float4 *>(p.gx + (((size_t)tl.unit * p.S + station) * p.T + t) * 2) = o;
                 }
                 __syncwarp();
             }
@@ -203,35 +267,46 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
         // ------------------------------------------------------------ MMA
         if (lane == 0) {
             constexpr uint32_t ID = idesc_tf32_f32(IG_M, IG_N);
+            long long g = 0;
             bool ok = true;
-            for (int kb = 0; kb < KB && ok; ++kb) {
-                const int s = kb % IG_STAGES;
-                if (!mbar_wait_bounded(&bars->full[s], (kb / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
-                    ok = false;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait_bounded(&bars->acc_empty[b], (uint32_t)((i >> 1) - 1) & 1, abort_flag,
+                                                 p.err, p.wait_ns))
                     break;
-                }
                 tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * IG_N);
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int s = (int)(g % IG_STAGES);
+                    if (!mbar_wait_bounded(&bars->full[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err,
+                                           p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint32_t o = 32u * ks;   // 8 tf32 of K per step
-                    tc_mma_tf32(tmem, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_hi(s) + o), ID,
-                                (kb | ks) ? 1u : 0u);
-                    tc_mma_tf32(tmem, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_lo(s) + o), ID, 1u);
-                    tc_mma_tf32(tmem, smem_desc_sw128(a_lo(s) + o), smem_desc_sw128(b_hi(s) + o), ID, 1u);
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t o = 32u * ks;   // 8 tf32 of K per step
+                        tc_mma_tf32(acc, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_hi(s) + o), ID,
+                                    (kb | ks) ? 1u : 0u);
+                        tc_mma_tf32(acc, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_lo(s) + o), ID, 1u);
+                        tc_mma_tf32(acc, smem_desc_sw128(a_lo(s) + o), smem_desc_sw128(b_hi(s) + o), ID, 1u);
+                    }
+                    tc_commit(&bars->empty[s]);
                 }
-                tc_commit(&bars->empty[s]);
+                if (ok) tc_commit(&bars->acc_full[b]);
             }
-            // the epilogue starts once every MMA has completed; on a give-up
-            // the same commit tells when TMEM may be freed (fixed 2 s bound)
-            tc_commit(&bars->acc_full);
+            // before TMEM is freed every MMA issued must have completed
+            // (fixed 2 s bound)
+            tc_commit(&bars->done);
             int dummy = 0;
-            mbar_wait_bounded(&bars->acc_full, 0, &dummy, p.err, 2000000000ull);
+            mbar_wait_bounded(&bars->done, 0, &dummy, p.err, 2000000000ull);
         }
         __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == 9) {
         tc_fence_after();
         tmem_dealloc(tmem, IG_TMEM_COLS);
     }
@@ -241,19 +316,17 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
 
 cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s)
 {
-    if (p.T <= 0) return cudaSuccess;
+    if (p.T <= 0 || p.units <= 0) return cudaSuccess;
     const size_t smem = ig_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(input_grad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // at most 65535 units per launch (the grid's z dimension)
-    for (int u0 = 0; u0 < p.units; u0 += 65535) {
-        IgParams q = p;
-        q.unit0 = u0;
-        dim3 grid((unsigned)((p.T + IG_N - 1) / IG_N), (unsigned)p.m_tiles, (unsigned)std::min(65535, p.units - u0));
-        input_grad_tc_kernel<<<grid, IG_THREADS, smem, s>>>(*static_cast<const CUtensorMap *>(xmap), q);
-        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long n_tiles = (long long)((p.T + IG_N - 1) / IG_N) * p.m_tiles * p.units;
+    const unsigned grid = (unsigned)std::min<long long>(n_tiles, std::max(1, sms));
+    input_grad_tc_kernel<<<grid, IG_THREADS, smem, s>>>(*static_cast<const CUtensorMap *>(xmap), p);
+    return cudaGetLastError();
 }
 
 } // namespace corr

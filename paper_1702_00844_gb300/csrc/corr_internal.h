@@ -48,10 +48,17 @@ struct IgParams {
     const float *at;          // A' tiles [unit][m tile][k block][hi, lo][128 x 32 floats]
     float2 *gx;               // [unit][S][T][2] complex
     int S, T, units, m_tiles, k_blocks;
-    int unit0;                // first unit of this launch (blockIdx.z counts from it)
     int *err;
     unsigned long long wait_ns;
 };
+// Times per tile of the tensor-core input gradient (its N) and operand
+// stages of its ring.
+#ifndef CORR_IG_N
+#define CORR_IG_N 128
+#endif
+#ifndef CORR_IG_STAGES
+#define CORR_IG_STAGES 3
+#endif
 // Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
 __host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
 __host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }
