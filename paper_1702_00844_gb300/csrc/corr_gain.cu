@@ -83,17 +83,17 @@ __global__ void sum_partials_kernel(const float *partial, int n, float *loss)
     if (threadIdx.x == 0) *loss = red[0];
 }
 
-// tf32 split of an FP32 value (corr_gain_tc.cu): hi = the value rounded to
-// tf32, lo = value - hi (exact in FP32) rounded to tf32.
-
 // Writes W'cb = v into the tensor-core input gradient's A' tiles: rows 2c
-// (re) and 2c+1 (im) of M', columns 2b (x re) and 2b+1 (x im) of K', each
-// value as hi and lo in the 128-byte swizzled K-major layout (row r at r x
-// 128 B, 16-byte chunk q at (q ^ (r % 8)) x 16 B).
+// (re) and 2c+1 (im) of M', columns 2b (x re) and 2b+1 (x im) of K', in the
+// 128-byte swizzled K-major layout (row r at r x 128 B, 16-byte chunk q at
+// (q ^ (r % 8)) x 16 B). With CORR_IG_A_FP32 the values are stored as they
+// are (the kernel splits them in shared memory); otherwise as hi = the value
+// rounded to tf32 and lo = (value - hi) rounded to tf32, in two tiles.
 __device__ __forceinline__ void store_w_tiles(float *at, int unit, int S, int c, int b, float2 v)
 {
+    constexpr int PARTS = CORR_IG_A_FP32 ? 1 : 2;
     const int mt = (2 * c) / 128, r = (2 * c) % 128, kb = (2 * b) / 32, kk = (2 * b) % 32;
-    const size_t tile = (((size_t)unit * ig_m_tiles(S) + mt) * ig_k_blocks(S) + kb) * 2;   // hi; lo = tile + 1
+    const size_t tile = (((size_t)unit * ig_m_tiles(S) + mt) * ig_k_blocks(S) + kb) * PARTS;
     const int q = kk >> 2;
     const float vals[2][2] = {{v.x, -v.y}, {v.y, v.x}};   // rows r (re) and r + 1 (im)
 #pragma unroll
@@ -101,9 +101,14 @@ __device__ __forceinline__ void store_w_tiles(float *at, int unit, int S, int c,
         const int rr = r + h;
         const size_t off = (size_t)rr * 32 + (size_t)((q ^ (rr & 7)) << 2) + (kk & 3);
         const float a0 = vals[h][0], a1 = vals[h][1];
-        const float h0 = tf32_round(a0), h1 = tf32_round(a1);
-        *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(h0, h1);
-        *reinterpret_cast<float2 *>(at + (tile + 1) * 4096 + off) = make_float2(tf32_round(a0 - h0), tf32_round(a1 - h1));
+        if (PARTS == 1) {
+            *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(a0, a1);
+        } else {
+            const float h0 = tf32_round(a0), h1 = tf32_round(a1);
+            *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(h0, h1);
+            *reinterpret_cast<float2 *>(at + (tile + 1) * 4096 + off) =
+                make_float2(tf32_round(a0 - h0), tf32_round(a1 - h1));
+        }
     }
 }
 

@@ -21,12 +21,13 @@
 // one persistent CTA per SM. Per K-block of 32 reduction values (8 stations
 // x 2 pols x re/im), through a ring of operand stages that runs on across
 // the CTA's tiles:
-//   - one thread issues the loads: A_hi and A_lo as 16 KB bulk copies of
-//     tiles that the gain-gradient kernel wrote already split and swizzled,
-//     and the samples with one TMA box of IG_N times (16 bytes each, 2 IG_N
+//   - one thread issues the loads: A' as 16 KB bulk copies of tiles that
+//     the gain-gradient kernel wrote already swizzled, split into hi and lo
+//     (or in FP32 with CORR_IG_A_FP32, split here in shared memory), and the
+//     samples with one TMA box of IG_N times (16 bytes each, 2 IG_N
 //     8-byte elements: one contiguous run) x 8 stations, landing
 //     station-major in the lo tile;
-//   - 128 threads split the samples into hi and lo and transpose them into
+//   - IG_SW warps split the samples into hi and lo and transpose them into
 //     K-major rows (one time each) of 8 stations x 16 bytes, the chunk of
 //     station j in row t at 16-byte position j ^ (t mod 8): the 128-byte
 //     swizzled layout the MMA reads;
@@ -46,9 +47,13 @@ namespace corr {
 
 namespace {
 
-// warp 0 loads, warps 1-4 split, warps 5-8 store (TMEM lane quarters 1, 2,
-// 3, 0), warp 9 allocates TMEM and issues the MMAs
-constexpr int IG_THREADS = 320;
+// warp 0 loads, warps 1 .. SW split, the next four store (each a different
+// TMEM lane quarter, warp % 4), the last allocates TMEM and issues the MMAs
+constexpr int IG_SW = CORR_IG_SPLIT_WARPS;
+constexpr int IG_SPLIT_THREADS = 32 * IG_SW;
+constexpr int IG_EPI_WARP0 = 1 + IG_SW, IG_MMA_WARP = IG_EPI_WARP0 + 4;
+constexpr int IG_THREADS = 32 * (IG_MMA_WARP + 1);
+constexpr int IG_A_PARTS = CORR_IG_A_FP32 ? 1 : 2;   // A' tiles per K block in global memory
 constexpr int IG_M = 128, IG_N = CORR_IG_N;    // tile: rows of M' x times
 constexpr int IG_STAGES = CORR_IG_STAGES;
 constexpr uint32_t IG_A_BYTES = IG_M * 128;      // 16 KB: 128 rows x 32 tf32
@@ -60,8 +65,8 @@ static_assert(IG_N == 64 || IG_N == 128, "input-gradient tile width (a TMA box r
 
 struct IgBars {
     uint64_t raw[IG_STAGES];     // loads landed (transaction bytes)
-    uint64_t rd[IG_STAGES];      // raw samples read into registers (128 arrivals)
-    uint64_t full[IG_STAGES];    // samples split (128 arrivals)
+    uint64_t rd[IG_STAGES];      // raw samples read into registers (one arrival per split thread)
+    uint64_t full[IG_STAGES];    // operands split (one arrival per split thread)
     uint64_t empty[IG_STAGES];   // MMAs of the stage done (commit)
     uint64_t acc_full[2];        // a tile's MMAs done (commit)
     uint64_t acc_empty[2];       // a tile's accumulator read out (4 warps)
@@ -110,8 +115,8 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
         prefetch_tmap(&xmap);
         for (int s = 0; s < IG_STAGES; ++s) {
             mbar_init(&bars->raw[s], 1);
-            mbar_init(&bars->rd[s], 128);
-            mbar_init(&bars->full[s], 128);
+            mbar_init(&bars->rd[s], IG_SPLIT_THREADS);
+            mbar_init(&bars->full[s], IG_SPLIT_THREADS);
             mbar_init(&bars->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
         bars->abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 9) {
+    if (warp == IG_MMA_WARP) {
         tmem_alloc(&bars->tmem_base, IG_TMEM_COLS);
         tmem_relinquish();
     }
@@ -142,9 +147,9 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
             bool ok = true;
             for (int i = 0; i < my_tiles && ok; ++i) {
                 const IgTile tl = ig_tile(blockIdx.x + (long long)i * gridDim.x, n_times, p);
-                // A' tiles of this (unit, row tile): [k block][hi, lo][128 rows x 128 B]
+                // A' tiles of this (unit, row tile): [k block][parts][128 rows x 128 B]
                 const uint8_t *a_tiles = reinterpret_cast<const uint8_t *>(p.at) +
-                                         ((size_t)tl.unit * p.m_tiles + tl.mt) * (size_t)KB * 2 * IG_A_BYTES;
+                                         ((size_t)tl.unit * p.m_tiles + tl.mt) * (size_t)KB * IG_A_PARTS * IG_A_BYTES;
                 for (int kb = 0; kb < KB; ++kb, ++g) {
                     const int s = (int)(g % IG_STAGES);
                     if (g >= IG_STAGES && !mbar_wait_bounded(&bars->empty[s], (uint32_t)((g / IG_STAGES) - 1) & 1,
@@ -152,10 +157,12 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&bars->raw[s], 2 * IG_A_BYTES + IG_B_BYTES);
-                    bulk_load_g2s(a_hi(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES, IG_A_BYTES, &bars->raw[s]);
-                    bulk_load_g2s(a_lo(s), a_tiles + (size_t)kb * 2 * IG_A_BYTES + IG_A_BYTES, IG_A_BYTES,
+                    mbar_arrive_expect_tx(&bars->raw[s], IG_A_PARTS * IG_A_BYTES + IG_B_BYTES);
+                    bulk_load_g2s(a_hi(s), a_tiles + (size_t)kb * IG_A_PARTS * IG_A_BYTES, IG_A_BYTES,
                                   &bars->raw[s]);
+                    if (IG_A_PARTS == 2)
+                        bulk_load_g2s(a_lo(s), a_tiles + ((size_t)kb * 2 + 1) * IG_A_BYTES, IG_A_BYTES,
+                                      &bars->raw[s]);
                     // the 8 stations of this K block, IG_N times from the
                     // tile's first (zero outside), into the lo tile
                     tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES + IG_B_BYTES, &xmap,
@@ -172,9 +179,9 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
             }
         }
         __syncwarp();
-    } else if (warp <= 4) {
+    } else if (warp <= IG_SW) {
         // ------------------------------------------------------------ split
-        const int pt = tid - 32;   // 0 .. 127
+        const int pt = tid - 32;   // 0 .. IG_SPLIT_THREADS - 1
         long long g = 0;
         bool ok = true;
         for (int i = 0; i < my_tiles && ok; ++i) {
@@ -184,23 +191,42 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                     ok = false;
                     break;
                 }
-                // chunk i = q * 128 + pt of the raw box (landed in the lo
-                // tile) is (station i / IG_N, time i % IG_N): consecutive
-                // threads read consecutive times of one station. Once all
-                // 128 threads hold their chunks (rd), each writes hi and lo
-                // into row t at 16-byte position (station ^ (t mod 8)).
-                constexpr int CH = IG_N / 16;   // chunks per thread
+                // chunk i = q * IG_SPLIT_THREADS + pt of the raw box (landed
+                // in the lo tile) is (station i / IG_N, time i % IG_N):
+                // consecutive threads read consecutive times of one station.
+                // Once all split threads hold their chunks (rd), each writes
+                // hi and lo into row t at 16-byte position (station ^ (t mod 8)).
+                constexpr int CH = IG_N * 8 / IG_SPLIT_THREADS;   // chunks per thread
                 uint4 v[CH];
 #pragma unroll
-                for (int q = 0; q < CH; ++q) v[q] = lds128(b_lo(s) + (uint32_t)((q * 128 + pt) * 16));
+                for (int q = 0; q < CH; ++q)
+                    v[q] = lds128(b_lo(s) + (uint32_t)((q * IG_SPLIT_THREADS + pt) * 16));
                 mbar_arrive(&bars->rd[s]);
+                // meanwhile, with FP32 A' tiles, A': each thread splits its
+                // own 16-byte chunks in place (hi) and into the lo tile at the
+                // same offset
+#pragma unroll
+                for (int q = 0; q < (IG_A_PARTS == 1 ? (int)(IG_A_BYTES / 16) / IG_SPLIT_THREADS : 0); ++q) {
+                    const uint32_t off = (uint32_t)((q * IG_SPLIT_THREADS + pt) * 16);
+                    const uint4 a = lds128(a_hi(s) + off);
+                    const float4 f = make_float4(__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z),
+                                                 __uint_as_float(a.w));
+                    const float4 hf =
+                        make_float4(tf32_round(f.x), tf32_round(f.y), tf32_round(f.z), tf32_round(f.w));
+                    sts128(a_hi(s) + off, make_uint4(__float_as_uint(hf.x), __float_as_uint(hf.y),
+                                                     __float_as_uint(hf.z), __float_as_uint(hf.w)));
+                    sts128(a_lo(s) + off, make_uint4(__float_as_uint(tf32_round(f.x - hf.x)),
+                                                     __float_as_uint(tf32_round(f.y - hf.y)),
+                                                     __float_as_uint(tf32_round(f.z - hf.z)),
+                                                     __float_as_uint(tf32_round(f.w - hf.w))));
+                }
                 if (!mbar_wait_bounded(&bars->rd[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
                     ok = false;
                     break;
                 }
 #pragma unroll
                 for (int q = 0; q < CH; ++q) {
-                    const int i = q * 128 + pt, st = i / IG_N, t = i % IG_N;
+                    const int i = q * IG_SPLIT_THREADS + pt, st = i / IG_N, t = i % IG_N;
                     const float4 f = make_float4(__uint_as_float(v[q].x), __uint_as_float(v[q].y),
                                                  __uint_as_float(v[q].z), __uint_as_float(v[q].w));
                     const float4 hf =
@@ -218,7 +244,7 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                 mbar_arrive(&bars->full[s]);
             }
         }
-    } else if (warp <= 8) {
+    } else if (warp < IG_MMA_WARP) {
         // --------------------------------------------------------- epilogue
         // TMEM lanes of this warp: 32 * (warp % 4) ..; lane r of the tile
         // is row m = 128 mt + r of M': c = m / 2 = (station, pol), and re
@@ -306,7 +332,7 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == IG_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tmem, IG_TMEM_COLS);
     }

@@ -45,7 +45,7 @@ cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, 
 // by gain_grad_launch in tile mode, samples through a TMA map of boxes of
 // 4 floats x 8 stations x 256 times (128-byte swizzle).
 struct IgParams {
-    const float *at;          // A' tiles [unit][m tile][k block][hi, lo][128 x 32 floats]
+    const float *at;          // A' tiles [unit][m tile][k block]([hi, lo] unless CORR_IG_A_FP32)[128 x 32 floats]
     float2 *gx;               // [unit][S][T][2] complex
     int S, T, units, m_tiles, k_blocks;
     int *err;
@@ -59,12 +59,21 @@ struct IgParams {
 #ifndef CORR_IG_STAGES
 #define CORR_IG_STAGES 3
 #endif
+// Warps that split the operands into tf32 hi and lo.
+#ifndef CORR_IG_SPLIT_WARPS
+#define CORR_IG_SPLIT_WARPS 4
+#endif
+// 1: A' tiles hold W' in FP32 and the kernel splits them in shared memory;
+// 0: the gain-gradient kernel writes them already split (hi and lo tiles).
+#ifndef CORR_IG_A_FP32
+#define CORR_IG_A_FP32 0
+#endif
 // Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
 __host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
 __host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }
 inline size_t ig_tile_bytes(int S, long long units)
 {
-    return (size_t)units * ig_m_tiles(S) * ig_k_blocks(S) * 2 * 16384;
+    return (size_t)units * ig_m_tiles(S) * ig_k_blocks(S) * (CORR_IG_A_FP32 ? 1 : 2) * 16384;
 }
 cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s);
 // tiles = 1: W is the A' tile buffer (zeroed once, its padding never written)
