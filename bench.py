@@ -219,6 +219,125 @@ def cpu_baseline(target_s: float = 12.0):
                       f"1024 samples each), FP64, {dt:.1f} s"}
 
 
+def _rel_frob(got, ref):
+    """Largest per-unit relative Frobenius error."""
+    import numpy as np
+    g = got.reshape(got.shape[0], -1)
+    r = ref.reshape(ref.shape[0], -1)
+    den = np.linalg.norm(r, axis=1)
+    return float((np.linalg.norm(g - r, axis=1) / np.where(den == 0, 1.0, den)).max())
+
+
+def _coef_err(got, ref, S):
+    """max |V - V_ref| / sqrt(V_ref_aa V_ref_bb): the error in the
+    normalised correlation coefficient."""
+    import numpy as np
+    auto = np.array([s * (s + 1) // 2 + s for s in range(S)])
+    a = np.stack([ref[:, auto, 0, 0].real, ref[:, auto, 1, 1].real], axis=-1)
+    s2 = np.concatenate([np.full(j + 1, j) for j in range(S)])
+    s1 = np.concatenate([np.arange(j + 1) for j in range(S)])
+    na = np.sqrt(np.maximum(a[:, s1, :], 1e-300))
+    nb = np.sqrt(np.maximum(a[:, s2, :], 1e-300))
+    return float((np.abs(got - ref) / (na[:, :, :, None] * nb[:, :, None, :])).max())
+
+
+def oracle_errors(torch):
+    """Errors against the FP64 oracle, stated per workload, on sampled
+    channels of host-generated data: the precision workload on the int8
+    (mismatched elements), f16 and FP32 paths; the production FP32 workload;
+    sub-arrays of the ragged batch in one batched f16 call; and the
+    differentiation workload's loss and gradients."""
+    import numpy as np
+
+    import oracle
+    import synth
+    from paper_1702_00844_gb300 import FLAG_GAINS, Plan
+    res = {}
+
+    def vis(t):
+        a = t.detach().cpu().numpy()
+        if a.dtype == np.int32:
+            return a.astype(np.int64)
+        return a.astype(np.complex128).reshape((-1,) + a.shape[-3:])
+
+    # precision: channels 0, 137, 479
+    picks = [0, 137, 479]
+    x8 = synth.precision(channels=picks)["x"]
+    ref = oracle.correlate(x8, "ci8")
+    p8 = Plan(S3, len(picks), T3, dtype="ci8", path="tensor")
+    got8 = vis(p8.correlate(torch.from_numpy(x8).cuda())).reshape(ref.shape + (2,))
+    mism = int((got8[..., 0] != ref.real.astype(np.int64)).sum() + (got8[..., 1] != ref.imag.astype(np.int64)).sum())
+    res["precision_int8"] = {"channels": picks, "mismatched_elements": mism, "elements": int(ref.size * 2)}
+    p16 = Plan(S3, len(picks), T3, dtype="cf16", path="tensor")
+    got16 = vis(p16.correlate(torch.from_numpy(synth.int8_as_cf16(x8)).cuda()))
+    res["precision_f16"] = {"channels": picks, "rel_frobenius_max": _rel_frob(got16, ref),
+                            "coef_error_max": _coef_err(got16, ref, S3), "bound": "2e-3 relative"}
+    xc = (x8[..., 0].astype(np.float32) + 1j * x8[..., 1].astype(np.float32)).astype(np.complex64)
+    p32 = Plan(S3, len(picks), T3, dtype="cf32", path="fp32")
+    got32 = vis(p32.correlate(torch.from_numpy(xc).cuda()))
+    res["precision_fp32"] = {"channels": picks, "rel_frobenius_max": _rel_frob(got32, ref),
+                             "coef_error_max": _coef_err(got32, ref, S3), "bound": "1e-5 relative"}
+    del p8, p16, p32
+    # production (one integration of 256 channels): channels 0, 100, 255
+    xp = synth.production(n_integrations=1)["x"][0]
+    pp = Plan(64, xp.shape[0], xp.shape[2], dtype="cf32", path="fp32")
+    gotp = vis(pp.correlate(torch.from_numpy(xp).cuda()))
+    cp = [0, 100, 255]
+    refp = oracle.correlate(xp[cp])
+    res["production_fp32"] = {"channels": cp, "rel_frobenius_max": _rel_frob(gotp[cp], refp),
+                              "coef_error_max": _coef_err(gotp[cp], refp, 64), "bound": "1e-5 relative"}
+    del pp, xp
+    # ragged batch: three sub-arrays (the smallest, a long integration and a
+    # partial last block) in one batched f16 call; two channels each
+    shapes = synth.batching_shapes()
+    pick = [min(range(len(shapes)), key=lambda k: shapes[k][0] * shapes[k][1] * shapes[k][2]),
+            next(k for k, s in enumerate(shapes) if s[2] >= 3000 and s[0] < 120),
+            next(k for k, s in enumerate(shapes) if s[0] % 64 and 120 < s[0] < 200)]
+    subs, outs, sh = [], [], []
+    for k in pick:
+        S, C, T = shapes[k]
+        subs.append(synth.batching_subarray_device(S, C, T, k, "cuda"))
+        outs.append(torch.empty((C, S * (S + 1) // 2, 2, 2), dtype=torch.complex64, device="cuda"))
+        sh.append((S, C, T))
+    pb = Plan(1, 1, 1, dtype="cf16", path="tensor")
+    pb.correlate_batched(list(zip(subs, outs)), sh)
+    torch.cuda.synchronize()
+    worst_f, worst_c = 0.0, 0.0
+    for (S, C, T), xs, o in zip(sh, subs, outs):
+        for c in (0, C - 1):
+            xh = xs[c].cpu().numpy()
+            r = oracle.correlate(xh[None], "cf16")
+            g = o[c].cpu().numpy().astype(np.complex128)[None]
+            worst_f = max(worst_f, _rel_frob(g, r))
+            worst_c = max(worst_c, _coef_err(g, r, S))
+    res["ragged_f16"] = {"sub_arrays": [list(s) for s in sh], "channels": "first and last of each",
+                         "rel_frobenius_max": worst_f, "coef_error_max": worst_c, "bound": "2e-3 relative"}
+    del subs, outs, pb
+    # differentiation: loss and gradients on channels 0, 31, 63
+    d = synth.differentiation()
+    pg = Plan(d["S"], d["C"], d["T"], dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    xd, gd, Md = (torch.from_numpy(d[k]).cuda() for k in ("x", "g", "M"))
+    R = pg.correlate(xd)
+    loss = torch.empty((), dtype=torch.float32, device="cuda")
+    gg, gx = pg.gain_backward(xd, gd, Md, R=R, loss=loss)
+    torch.cuda.synchronize()
+    gg, gx = gg.cpu().numpy(), gx.cpu().numpy()
+    Lref, _ = oracle.gain_loss(oracle.correlate(d["x"]), d["g"], d["M"])
+    eg, ex = 0.0, 0.0
+    for c in (0, 31, 63):
+        Rc = oracle.correlate(d["x"][c][None])
+        gr = oracle.gain_grad(Rc, d["g"][c][None], d["M"][c][None])
+        xr = oracle.input_grad(d["x"][c][None], Rc, d["g"][c][None], d["M"][c][None])
+        eg = max(eg, float(np.abs(gg[c][None] - gr).max() / np.abs(gr).max()))
+        ex = max(ex, float(np.abs(gx[c][None] - xr).max() / np.abs(xr).max()))
+    res["differentiation_fp32"] = {"channels": [0, 31, 63], "loss_rel": abs(float(loss) - Lref) / Lref,
+                                   "grad_gain_max_rel": eg, "grad_samples_max_rel": ex,
+                                   "bound": "1e-4 (gradients)"}
+    del pg
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_fp32_correlator(target_s: float = 6.0):
     """The multithreaded FP32 CPU correlator (Section 4.1's design) on the
     precision workload's samples as complex64: channels sized from a first
@@ -630,6 +749,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu and wl == "precision":
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_fp32_correlator"] = cpu_fp32_correlator()
+        line["oracle_errors"] = oracle_errors(torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -67,3 +67,33 @@ def test_bench_ops_count_and_profile_link():
     assert float(keys["dram_bytes_per_launch_full"]) > 0
     peaks, src = bench.measured_peaks()
     assert src in ("measured", "fallback") and peaks["hbm_gbs"] > 0
+
+
+def test_bench_ragged_mode_and_error_metrics():
+    """--workload ragged with --ragged-scale keeps every sub-array and
+    scales its channels (at least one each); the error metrics the bench
+    reports against the oracle are the plain definitions."""
+    import numpy as np
+
+    import bench
+    import synth
+    a = bench.parse(["--workload", "ragged", "--ragged-scale", "0.05"])
+    assert a.workload == "ragged" and a.ragged_scale == 0.05
+    full = synth.batching_shapes()
+    small = bench.ragged_shapes(0.05)
+    assert [(s, t) for s, _, t in small] == [(s, t) for s, _, t in full]
+    assert all(c == max(1, round(C * 0.05)) for (_, c, _), (_, C, _) in zip(small, full))
+    assert bench.ragged_shapes(1.0) == full
+    # relative Frobenius error per unit, the largest over units
+    ref = np.ones((2, 3, 2, 2), dtype=np.complex128)
+    got = ref.copy()
+    got[1, 0, 0, 0] += 0.5
+    assert abs(bench._rel_frob(got, ref) - 0.5 / np.sqrt(12)) < 1e-12
+    # correlation-coefficient error: |dV_ab| / sqrt(V_aa V_bb); 2 stations
+    S = 2
+    ref = np.zeros((1, 3, 2, 2), dtype=np.complex128)
+    ref[0, 0, 0, 0] = ref[0, 0, 1, 1] = 4.0     # station 0 autocorrelations
+    ref[0, 2, 0, 0] = ref[0, 2, 1, 1] = 9.0     # station 1
+    got = ref.copy()
+    got[0, 1, 0, 1] += 1.2                      # baseline (0, 1), X x Y
+    assert abs(bench._coef_err(got, ref, S) - 1.2 / 6.0) < 1e-12
