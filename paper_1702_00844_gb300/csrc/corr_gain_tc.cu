@@ -255,8 +255,10 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
         const int k = lane & 3, quad = lane & ~3;
         for (int i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!mbar_wait_bounded(&bars->acc_full[b], (uint32_t)(i >> 1) & 1, abort_flag, p.err, p.wait_ns))
-                break;
+            // the warp leaves together (the TMEM loads below are warp-wide)
+            const bool got =
+                mbar_wait_bounded(&bars->acc_full[b], (uint32_t)(i >> 1) & 1, abort_flag, p.err, p.wait_ns);
+            if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
             const IgTile tl = ig_tile(blockIdx.x + (long long)i * gridDim.x, n_times, p);
             const int station = (IG_M * tl.mt + quarter * 32) / 4 + (lane >> 2);

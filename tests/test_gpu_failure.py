@@ -69,3 +69,44 @@ def test_fp32_tiny_wait_limit_is_safe(monkeypatch):
     ref = oracle.correlate(d["x"])
     got = out.cpu().numpy().reshape(ref.shape)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_input_gradient_wait_timeout_is_reported_and_context_survives(monkeypatch):
+    """The tensor-core input gradient with a 1 ns wait limit, on 1024
+    stations (128 K-blocks per tile, so that the epilogue waits about 100 us
+    for a tile's MMAs): its roles give up on their first wait that does not
+    complete at once; the loader waits for its copies in flight and the MMA
+    thread for its MMAs before TMEM is freed. The host sees
+    CORR_ERR_TIMEOUT, and a plan with the default limit afterwards matches
+    the oracle."""
+    from paper_1702_00844_gb300 import FLAG_GAINS, CorrError, Plan
+    S, C, T = 1024, 2, 256
+    B = S * (S + 1) // 2
+    x = torch.zeros((C, S, T, 2), dtype=torch.complex64, device="cuda")
+    g = torch.ones((C, S, 2), dtype=torch.complex64, device="cuda")
+    R = torch.zeros((C, B, 2, 2), dtype=torch.complex64, device="cuda")
+    M = torch.zeros_like(R)
+    monkeypatch.setenv("CORR_WAIT_LIMIT_NS", "1")
+    plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    plan.gain_backward(x, g, M, R=R)
+    torch.cuda.synchronize()          # the kernels ended by themselves
+    with pytest.raises(CorrError) as e:
+        plan.check_error()
+    assert e.value.status == 5
+    plan.check_error()
+
+    monkeypatch.delenv("CORR_WAIT_LIMIT_NS")
+    S2, C2, T2 = 40, 3, 300
+    rg = synth.rng(97)
+    xh = synth.complex_normal(rg, (C2, S2, T2, 2))
+    gains = (1 + synth.complex_normal(rg, (C2, S2, 2), sigma=0.1)).astype(np.complex64)
+    Mh = synth.sky_model(C2, S2, T2, rg).astype(np.complex64)
+    xd, gd, Md = (torch.from_numpy(a).cuda() for a in (xh, gains, Mh))
+    good = Plan(S2, C2, T2, dtype="cf32", path="fp32", flags=FLAG_GAINS)
+    _, gx = good.gain_backward(xd, gd, Md)
+    torch.cuda.synchronize()
+    good.check_error()
+    Rref = oracle.correlate(xh)
+    ref = oracle.input_grad(xh, Rref, gains, Mh)
+    got = gx.cpu().numpy().astype(np.complex128)
+    assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max()
