@@ -141,8 +141,8 @@ corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, in
 
 // The samples for the tensor-core input gradient as 8-byte elements (one
 // complex float each, copied bit for bit): dims (2T per station, stations,
-// units, 1), boxes of 2 CORR_IG_N elements x 8 stations: one contiguous run
-// of CORR_IG_N x 16 bytes per station, landing station-major. No swizzle
+// units, 1), boxes of 2 CORR_IG_BOX elements x 8 stations: one contiguous
+// run of CORR_IG_BOX x 16 bytes per station, landing station-major. No swizzle
 // mode; the kernel transposes and swizzles.
 corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long long units)
 {
@@ -153,7 +153,7 @@ corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long
     }
     cuuint64_t dims[4] = {2 * (cuuint64_t)T, (cuuint64_t)S, (cuuint64_t)units, 1};
     cuuint64_t strides[3] = {(cuuint64_t)T * 16, (cuuint64_t)S * T * 16, (cuuint64_t)units * S * T * 16};
-    cuuint32_t box[4] = {2 * CORR_IG_N, 8, 1, 1};
+    cuuint32_t box[4] = {2 * CORR_IG_BOX, 8, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(d_in), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -61,7 +61,9 @@ constexpr uint32_t IG_B_BYTES = IG_N * 128;      // IG_N rows x 32 tf32
 constexpr uint32_t IG_STAGE_BYTES = 2 * IG_A_BYTES + 2 * IG_B_BYTES;   // A hi, A lo, B hi, B lo
 constexpr uint32_t IG_EPI_BYTES = 4 * 32 * 17 * 4;                       // per-warp transpose
 constexpr uint32_t IG_TMEM_COLS = 2 * IG_N;      // two accumulators
-static_assert(IG_N == 64 || IG_N == 128, "input-gradient tile width (a TMA box row holds at most 256 elements)");
+constexpr int IG_BOX = CORR_IG_BOX;              // times per TMA box of samples
+static_assert(IG_N == 64 || IG_N == 128 || IG_N == 256, "input-gradient tile width");
+static_assert(IG_N % IG_BOX == 0 && 2 * IG_BOX <= 256, "a TMA box row holds at most 256 elements");
 
 struct IgBars {
     uint64_t raw[IG_STAGES];     // loads landed (transaction bytes)
@@ -164,9 +166,13 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                         bulk_load_g2s(a_lo(s), a_tiles + ((size_t)kb * 2 + 1) * IG_A_BYTES, IG_A_BYTES,
                                       &bars->raw[s]);
                     // the 8 stations of this K block, IG_N times from the
-                    // tile's first (zero outside), into the lo tile
-                    tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES + IG_B_BYTES, &xmap,
-                                &bars->raw[s], 2 * tl.nt * IG_N, kb * 8, tl.unit, 0);
+                    // tile's first (zero outside), into the lo tile: boxes of
+                    // IG_BOX times, each landing station-major
+#pragma unroll
+                    for (int h = 0; h < IG_N / IG_BOX; ++h)
+                        tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES + IG_B_BYTES +
+                                        (size_t)h * IG_BOX * 128,
+                                    &xmap, &bars->raw[s], 2 * (tl.nt * IG_N + h * IG_BOX), kb * 8, tl.unit, 0);
                 }
             }
             // on a give-up, let the copies in flight land before the CTA (and
@@ -191,9 +197,10 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                     ok = false;
                     break;
                 }
-                // chunk i = q * IG_SPLIT_THREADS + pt of the raw box (landed
-                // in the lo tile) is (station i / IG_N, time i % IG_N):
-                // consecutive threads read consecutive times of one station.
+                // chunk i = q * IG_SPLIT_THREADS + pt of the raw boxes
+                // (landed in the lo tile, box after box) is (station
+                // (i / IG_BOX) % 8, time of its box i % IG_BOX): consecutive
+                // threads read consecutive times of one station.
                 // Once all split threads hold their chunks (rd), each writes
                 // hi and lo into row t at 16-byte position (station ^ (t mod 8)).
                 constexpr int CH = IG_N * 8 / IG_SPLIT_THREADS;   // chunks per thread
@@ -226,7 +233,9 @@ __global__ void __launch_bounds__(IG_THREADS, 1)
                 }
 #pragma unroll
                 for (int q = 0; q < CH; ++q) {
-                    const int i = q * IG_SPLIT_THREADS + pt, st = i / IG_N, t = i % IG_N;
+                    // box h = i / (8 IG_BOX), station, time h IG_BOX + i % IG_BOX
+                    const int i = q * IG_SPLIT_THREADS + pt, st = (i / IG_BOX) % 8,
+                              t = (i / (8 * IG_BOX)) * IG_BOX + i % IG_BOX;
                     const float4 f = make_float4(__uint_as_float(v[q].x), __uint_as_float(v[q].y),
                                                  __uint_as_float(v[q].z), __uint_as_float(v[q].w));
                     const float4 hf =

@@ -52,13 +52,15 @@ struct IgParams {
     unsigned long long wait_ns;
 };
 // Times per tile of the tensor-core input gradient (its N) and operand
-// stages of its ring.
+// stages of its ring. A TMA box of samples holds at most CORR_IG_BOX times
+// (2 x CORR_IG_BOX 8-byte elements <= 256); wider tiles take several.
 #ifndef CORR_IG_N
 #define CORR_IG_N 128
 #endif
 #ifndef CORR_IG_STAGES
 #define CORR_IG_STAGES 3
 #endif
+#define CORR_IG_BOX (CORR_IG_N < 128 ? CORR_IG_N : 128)
 // Warps that split the operands into tf32 hi and lo.
 #ifndef CORR_IG_SPLIT_WARPS
 #define CORR_IG_SPLIT_WARPS 4
