@@ -502,6 +502,19 @@ def secondary(x8, torch):
     res["tensor_fp16_precision_sustained"] = {
         "ms": ms, "TOPS": ops3 / ms / 1e9, "steps": 2000, "clocks": clk.summary(),
         "frac_sustained": ops3 / ms / 1e9 / float(peaks.get("bf16_tflops_sustained", 1700.0))}
+    # the same shape on complex N(0,1) f16 samples, the ragged batch's value
+    # distribution (full mantissas: the tensor cores draw more power on them
+    # than on small integers), again for about a second
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 6)
+    xg = torch.randn(x16.shape, generator=gen, device="cuda", dtype=torch.float32).to(torch.float16)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_launches(lambda: p16.correlate(xg, o16), 2000, 3, st)
+    res["tensor_fp16_gaussian_sustained"] = {
+        "ms": ms, "TOPS": ops3 / ms / 1e9, "steps": 2000, "clocks": clk.summary(),
+        "frac_sustained": ops3 / ms / 1e9 / float(peaks.get("bf16_tflops_sustained", 1700.0)),
+        "data": "256 st. x 480 ch. x 1024, complex f16 N(0,1)"}
+    del xg
     del o16, x16, p16
     xc = torch.view_as_complex(x8.to(torch.float32).contiguous())
     p32 = Plan(S3, C3, T3, dtype="cf32", path="fp32")
