@@ -1323,9 +1323,11 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
     const float2 *M = static_cast<const float2 *>(d_vis_model);
     // The input gradient on the tensor cores (tf32 split, FP32 accuracy)
     // when the samples and the gradient are 16-byte aligned (TMA loads,
-    // 16-byte stores); otherwise, or with CORR_IG_PATH=cuda_core, the FP32
-    // CUDA-core GEMM.
+    // 16-byte stores), on CTA pairs when there are two row tiles or more;
+    // otherwise, or with CORR_IG_PATH=cuda_core, the FP32 CUDA-core GEMM.
+    // CORR_IG_PATH=tc1 keeps the tensor-core path on single CTAs.
     const char *ig = std::getenv("CORR_IG_PATH");
+    const bool ig_pair = ig_m_tiles(S) >= 2 && !(ig && std::strcmp(ig, "tc1") == 0);
     const bool tc = d_grad_in && h->d.n_samples > 0 && aligned16(d_in) &&
                     aligned16(d_grad_in) && !(ig && std::strcmp(ig, "cuda_core") == 0);
     CUtensorMap xmap{};
@@ -1345,10 +1347,11 @@ corr_status_t corr_gain_backward(corr_handle_t h, const void *d_in, const void *
         ip.T = h->d.n_samples;
         ip.units = units;
         ip.m_tiles = ig_m_tiles(S);
+        ip.m_alloc = ig_m_alloc(S);
         ip.k_blocks = ig_k_blocks(S);
         ip.err = h->d_err;
         ip.wait_ns = h->wait_ns;
-        e = cuda_status(input_grad_tc_launch(&xmap, ip, st));
+        e = cuda_status(input_grad_tc_launch(&xmap, ip, st, ig_pair));
         if (e != CORR_OK) return e;
     } else if (d_grad_in) {
         e = cuda_status(input_grad_launch(static_cast<const float2 *>(d_in), h->d_W,

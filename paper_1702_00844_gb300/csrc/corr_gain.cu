@@ -93,7 +93,7 @@ __device__ __forceinline__ void store_w_tiles(float *at, int unit, int S, int c,
 {
     constexpr int PARTS = CORR_IG_A_FP32 ? 1 : 2;
     const int mt = (2 * c) / 128, r = (2 * c) % 128, kb = (2 * b) / 32, kk = (2 * b) % 32;
-    const size_t tile = (((size_t)unit * ig_m_tiles(S) + mt) * ig_k_blocks(S) + kb) * PARTS;
+    const size_t tile = (((size_t)unit * ig_m_alloc(S) + mt) * ig_k_blocks(S) + kb) * PARTS;
     const int q = kk >> 2;
     const float vals[2][2] = {{v.x, -v.y}, {v.y, v.x}};   // rows r (re) and r + 1 (im)
 #pragma unroll

@@ -48,6 +48,7 @@ struct IgParams {
     const float *at;          // A' tiles [unit][m tile][k block]([hi, lo] unless CORR_IG_A_FP32)[128 x 32 floats]
     float2 *gx;               // [unit][S][T][2] complex
     int S, T, units, m_tiles, k_blocks;
+    int m_alloc;              // row tiles per unit in the A' buffer (m_tiles rounded up to even)
     int *err;
     unsigned long long wait_ns;
 };
@@ -73,11 +74,15 @@ struct IgParams {
 // Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
 __host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
 __host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }
+// A CTA pair takes two row tiles; with an odd count the second of the last
+// pair reads a zero tile.
+__host__ __device__ inline int ig_m_alloc(int S) { return (ig_m_tiles(S) + 1) & ~1; }
 inline size_t ig_tile_bytes(int S, long long units)
 {
-    return (size_t)units * ig_m_tiles(S) * ig_k_blocks(S) * (CORR_IG_A_FP32 ? 1 : 2) * 16384;
+    return (size_t)units * ig_m_alloc(S) * ig_k_blocks(S) * (CORR_IG_A_FP32 ? 1 : 2) * 16384;
 }
-cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s);
+// pair: tiles of two row tiles on CTA pairs (cta_group::2)
+cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s, bool pair);
 // tiles = 1: W is the A' tile buffer (zeroed once, its padding never written)
 cudaError_t gain_grad_launch(const float2 *R, const float2 *g, const float2 *M,
                              const float *scale, float2 *grad_g, void *W, int S, int units,

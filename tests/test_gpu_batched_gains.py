@@ -237,12 +237,14 @@ def _input_grad(plan, xd, gd, Md, R, grad_x):
 @pytest.mark.parametrize("S,C,T", [(8, 2, 64), (37, 2, 300), (70, 3, 700)])
 def test_input_gradient_tensor_and_cuda_core_paths_vs_oracle(S, C, T, monkeypatch):
     """dL/dx on the tensor cores (the default for 16-byte aligned buffers:
-    tf32 with each operand split into value and remainder) and on the CUDA
-    cores (CORR_IG_PATH=cuda_core), both against the oracle. The shapes span
-    one to three 128-row tiles of 4S, a K block that 4S fills only in part
-    (S = 37, 70) and a last time tile of fewer than 256 samples. 2e-5 of the
-    largest element is FP32-class accuracy: one unsplit tf32 product would
-    miss it by about two orders of magnitude."""
+    tf32 with each operand split into value and remainder; CTA pairs from two
+    row tiles on), on single CTAs (CORR_IG_PATH=tc1) and on the CUDA cores
+    (CORR_IG_PATH=cuda_core), all against the oracle. The shapes span one to
+    three 128-row tiles of 4S (three: a pair whose second row tile is
+    missing), a K block that 4S fills only in part (S = 37, 70) and a last
+    time tile of fewer than 128 or 256 samples. 2e-5 of the largest element
+    is FP32-class accuracy: one unsplit tf32 product would miss it by about
+    two orders of magnitude."""
     from paper_1702_00844_gb300 import FLAG_GAINS, Plan
     x, gains, M = gain_case(S, C, T, seed=90 + S)
     plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
@@ -252,11 +254,11 @@ def test_input_gradient_tensor_and_cuda_core_paths_vs_oracle(S, C, T, monkeypatc
     xref = oracle.input_grad(x, Rref, gains, M)
     scale = np.abs(xref).max()
     got = {}
-    for path in ("tensor", "cuda_core"):
-        if path == "cuda_core":
-            monkeypatch.setenv("CORR_IG_PATH", "cuda_core")
-        else:
+    for path in ("tensor", "tc1", "cuda_core"):
+        if path == "tensor":
             monkeypatch.delenv("CORR_IG_PATH", raising=False)
+        else:
+            monkeypatch.setenv("CORR_IG_PATH", path)
         got[path] = _input_grad(plan, xd, gd, Md, R, torch.full_like(xd, float("nan")))
         assert np.isfinite(got[path]).all(), path
         assert np.abs(got[path] - xref).max() < 2e-5 * scale, path
@@ -307,11 +309,11 @@ def test_input_gradient_beyond_65535_units(monkeypatch):
     plan = Plan(S, C, T, dtype="cf32", path="fp32", flags=FLAG_GAINS)
     xd, gd, Md = _dev(x), _dev(gains), _dev(M)
     R = plan.correlate(xd)
-    for path in ("tensor", "cuda_core"):
-        if path == "cuda_core":
-            monkeypatch.setenv("CORR_IG_PATH", "cuda_core")
-        else:
+    for path in ("tensor", "tc1", "cuda_core"):
+        if path == "tensor":
             monkeypatch.delenv("CORR_IG_PATH", raising=False)
+        else:
+            monkeypatch.setenv("CORR_IG_PATH", path)
         gx = _input_grad(plan, xd, gd, Md, R, torch.full_like(xd, float("nan")))
         assert np.isfinite(gx).all(), path
         for c in (0, 65534, 65535, C - 1):
