@@ -125,13 +125,14 @@ template <> struct Cfg<2, TC_PAIR> {
 };
 #endif
 
-// int8 pair tiles of two pols stage the epilogue's last column groups in
-// shared memory: STG groups of 8 column stations (4 KB per epilogue warp),
-// copied there raw from TMEM so that the accumulator is released sooner;
-// their conversion and global stores follow while the next tile's MMAs run.
-// The operand ring is one stage shorter to make room. Measured on 256
-// stations: 4 operand stages + 6 staged groups 1-1.5% faster than 6 stages
-// without staging (3 + 8: equal; f16 pair tiles: slower, so STG = 0 there).
+// int8 pair tiles stage the epilogue's last column groups in shared memory:
+// STG groups of 8 column (pseudo-)stations (4 KB per epilogue warp), copied
+// there raw from TMEM so that the accumulator is released sooner; their
+// conversion and global stores follow while the next tile's MMAs run. The
+// operand ring is one stage shorter to make room. Measured on 256 stations:
+// 4 operand stages + 6 staged groups 1-1.5% faster than 6 stages without
+// staging (3 + 8: equal; f16 pair tiles: slower, so STG = 0 there); one pol
+// (512 stations), 4% faster.
 #ifndef CORR_TC_OPS_STG_I8
 #define CORR_TC_OPS_STG_I8 4
 #endif
@@ -146,7 +147,7 @@ constexpr int STG_GROUP_BYTES = 8 * 512;  // per warp: 8 column stations x 32 ro
 // instantiation the autotuner can choose) keeps the six-stage operand ring
 // and stores every epilogue group directly.
 template <int DT, int V, int NPOL, int LY = 0> struct Lay {
-    static constexpr bool STAGED = V == TC_PAIR && NPOL == 2 && DT == 2 && LY == 0 && CORR_TC_STG_I8 > 0;
+    static constexpr bool STAGED = V == TC_PAIR && DT == 2 && LY == 0 && CORR_TC_STG_I8 > 0;
     static constexpr int STG = STAGED ? CORR_TC_STG_I8 : 0;
     static constexpr int OPS = STAGED ? CORR_TC_OPS_STG_I8 : Cfg<DT, V>::OPS;
     static constexpr int RAW = Cfg<DT, V>::RAW;
@@ -839,7 +840,7 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
                 // Re and Im. The first ndirect groups are stored to global
                 // memory from registers; the load of the next group overlaps
                 // the stores of the current one (two register sets). The last
-                // nst groups (int8 pair tiles of two pols, one chunk) are
+                // nst groups (int8 pair tiles, one chunk) are
                 // staged in this warp's shared-memory ring, so that the
                 // accumulator is released once they are there; their global
                 // writes then overlap the next tile's MMAs.
