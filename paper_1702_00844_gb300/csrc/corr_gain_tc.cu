@@ -28,7 +28,7 @@
 //   - one thread issues the loads: A' as 16 KB bulk copies of tiles that
 //     the gain-gradient kernel wrote already swizzled, split into hi and lo
 //     (or in FP32 with CORR_IG_A_FP32, split here in shared memory), and the
-//     samples with one TMA box of IG_N times (16 bytes each, 2 IG_N
+//     samples with TMA boxes of IG_BOX times (16 bytes each, 2 IG_BOX
 //     8-byte elements: one contiguous run) x 8 stations, landing
 //     station-major in the lo tile;
 //   - IG_SW warps split the samples into hi and lo and transpose them into
