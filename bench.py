@@ -53,11 +53,13 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["precision", "precision-f16", "production", "ragged"],
+    ap.add_argument("--workload", choices=["precision", "precision-f16", "production", "production-tf32",
+                                           "ragged"],
                     default="precision",
                     help="precision: int8 tensor path at 256 stations (the headline); "
                          "precision-f16: the same samples on the f16 tensor path; "
                          "production: the 64-station FP32 workload on the FP32 path; "
+                         "production-tf32: the same on the tensor cores (tf32 value + remainder split); "
                          "ragged: the 32-sub-array f16 batch alone")
     ap.add_argument("--ragged-scale", type=float, default=1.0,
                     help="channels of each ragged sub-array scaled by this factor")
@@ -286,7 +288,11 @@ def oracle_errors(torch):
     refp = oracle.correlate(xp[cp])
     res["production_fp32"] = {"channels": cp, "rel_frobenius_max": _rel_frob(gotp[cp], refp),
                               "coef_error_max": _coef_err(gotp[cp], refp, 64), "bound": "1e-5 relative"}
-    del pp, xp
+    ptt = Plan(64, xp.shape[0], xp.shape[2], dtype="cf32", path="tensor")
+    gott = vis(ptt.correlate(torch.from_numpy(xp).cuda()))
+    res["production_tf32_split"] = {"channels": cp, "rel_frobenius_max": _rel_frob(gott[cp], refp),
+                                    "coef_error_max": _coef_err(gott[cp], refp, 64), "bound": "1e-5 relative"}
+    del pp, ptt, xp
     # ragged batch: three sub-arrays (the smallest, a long integration and a
     # partial last block) in one batched f16 call; two channels each
     shapes = synth.batching_shapes()
@@ -521,7 +527,12 @@ def secondary(x8, torch):
     o32 = p32.empty_out()
     ms = time_launches(lambda: p32.correlate(xc, o32), 3, 1, st)
     res["fp32_cuda_core_precision"] = {"ms": ms, "TOPS": ops3 / ms / 1e9}
-    del o32, xc, p32
+    # the same FP32 samples on the tensor cores (tf32 value + remainder
+    # split, three products per term, FP32 accumulation)
+    pt = Plan(S3, C3, T3, dtype="cf32", path="tensor")
+    ms = time_launches(lambda: pt.correlate(xc, o32), 3, 1, st)
+    res["tensor_tf32_split_fp32_precision"] = {"ms": ms, "TOPS": ops3 / ms / 1e9}
+    del o32, xc, p32, pt
     torch.cuda.empty_cache()
     # production FP32 workload: 64 stations, 256 channels, 768 samples, 10 integrations
     S2, C2, T2, I2 = 64, 256, 768, 10
@@ -532,7 +543,10 @@ def secondary(x8, torch):
     o2 = p2.empty_out()
     ms = time_launches(lambda: p2.correlate(x2, o2), 5, 2, st)
     res["fp32_cuda_core_production"] = {"ms": ms, "TOPS": ops_of(S2, T2, C2 * I2) / ms / 1e9}
-    del x2, o2, p2
+    pt2 = Plan(S2, C2, T2, I2, dtype="cf32", path="tensor")
+    ms = time_launches(lambda: pt2.correlate(x2, o2), 5, 2, st)
+    res["tensor_tf32_split_fp32_production"] = {"ms": ms, "TOPS": ops_of(S2, T2, C2 * I2) / ms / 1e9}
+    del x2, o2, p2, pt2
     torch.cuda.empty_cache()
     # ragged batch: 32 sub-arrays, one persistent launch (graph replay)
     res["tensor_fp16_ragged_batch"] = ragged_batch(torch, steps=20)
@@ -603,22 +617,25 @@ def run_ours(args):
     dev = torch.cuda.current_device()
 
     wl = args.workload
+    prod = wl in ("production", "production-tf32")
     # this rank's channels of the workload (all of them unless --split channels)
-    c_lo, c_hi = rank_channels(args.split, 256 if wl == "production" else C3, world, rank)
+    c_lo, c_hi = rank_channels(args.split, 256 if prod else C3, world, rank)
     # weak scaling: a workload of its own per rank; strong: this rank's
     # share of the one workload
     split = args.split == "channels"
-    x8 = synth.precision_device(c_hi - c_lo if wl != "production" else C3, S3, T3, "cuda",
+    x8 = synth.precision_device(c_hi - c_lo if not prod else C3, S3, T3, "cuda",
                                 rank=0 if split else rank, first_channel=c_lo if split else 0)
-    if wl == "production":
+    if prod:
         S, C, T, I = 64, c_hi - c_lo, 768, 10
         gen = torch.Generator(device="cuda")
         gen.manual_seed(synth.BASE_SEED + 2 + 7919 * rank)
         x = torch.randn((I, C, S, T, 2), dtype=torch.complex64, device="cuda", generator=gen)
-        plan = Plan(S, C, T, I, dtype="cf32", path="fp32")
+        tf32 = wl == "production-tf32"
+        plan = Plan(S, C, T, I, dtype="cf32", path="tensor" if tf32 else "fp32")
         units, dtype_label = C * I, "f32"
         workload = ("production: 64 stations, 2 pols, 256 channels, 768 samples, 10 integrations, "
-                    "complex64 N(0,1), FP32 CUDA-core path")
+                    "complex64 N(0,1), " + ("tensor cores, tf32 value + remainder split" if tf32
+                                            else "FP32 CUDA-core path"))
     else:
         S, C, T, I = S3, c_hi - c_lo, T3, 1
         if wl == "precision-f16":
@@ -706,7 +723,14 @@ def run_ours(args):
     # redo launch (empty on this data)
     achieved = ops / (kernel_ms * 1e-3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    if wl == "production":
+    if wl == "production-tf32":
+        # tf32 dense (the measured bf16 rate x the nominal tf32 : bf16 ratio
+        # 1.1 : 2.25), divided by the three tf32 products per correlator term
+        peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25 / 3
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "tf32_correlate_kernel",
+                "peak_source": f"{peak_src} bf16 dense burst x 1.1/2.25 (tf32) / 3 (split products)"}
+    elif wl == "production":
         # FP32 FMA pipe: this device's SMs x 128 FP32 lanes x 2 flops x maximum SM clock
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -740,18 +764,21 @@ def run_ours(args):
                                       "FP32 sums by a station-power bound, chunked INT32 fold "
                                       "for tiles that fail it",
                                 "f16": "tcgen05 kind::f16, FP32 accumulation in TMEM",
-                                "f32": "FP32 CUDA cores, TMA-staged samples"}[dtype_label],
+                                "f32": "FP32 CUDA cores, TMA-staged samples"}[dtype_label]
+                       if wl != "production-tf32" else
+                       "tcgen05 kind::tf32, value + remainder split (three products per term), FP32 "
+                       "accumulation in TMEM in 256-sample chunks summed in FP32",
                        "l2": f"inputs {units * S * T * in_bps / 1e6:.0f} MB and outputs "
                              f"{units * S * (S + 1) // 2 * 32 / 1e6:.0f} MB; inputs exceed L2 "
                              "(129 MB): no flush",
                        "parallelism": (f"{world} GPU(s), the workload's channels split over them "
-                                       f"(this rank: {c_hi - c_lo} of {c_hi - c_lo if args.split == 'none' else (256 if wl == 'production' else C3)}), no collective"
+                                       f"(this rank: {c_hi - c_lo} of {c_hi - c_lo if args.split == 'none' else (256 if prod else C3)}), no collective"
                                        if args.split == "channels" else
                                        f"channels per GPU fixed, {world} GPU(s), no collective")},
             "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
             "tile_config": (dict(plan.tile_config(),
                                  tuned=[["/".join(map(str, c)), round(t, 4)] for c, t in plan.tune_results()])
-                            if wl != "production" else None),
+                            if not prod else None),
             # one tensor launch per step, plus the (usually empty) redo launch
             # of the int8 path when T exceeds one 512-sample chunk
             "gpu_launches": args.steps * (2 if dtype_label == "s8" and T > 512 else 1)}

@@ -66,7 +66,11 @@ typedef enum { CORR_CF32 = 0, CORR_CF16 = 1, CORR_CI8 = 2 } corr_dtype_t;
  *   CORR_PATH_FP32   : FP32 CUDA-core kernel (4 FMAs per complex multiply-add,
  *                      Section 2); inputs CORR_CF32 only.
  *   CORR_PATH_TENSOR : tcgen05 tensor-core kernel; CORR_CF16 (FP32
- *                      accumulation) or CORR_CI8 (exact, INT32 result).
+ *                      accumulation) or CORR_CI8 (exact, INT32 result); or
+ *                      CORR_CF32 with two pols: every sample split into a
+ *                      tf32 value and a tf32 remainder, three tf32 products
+ *                      per product term, FP32 accumulation (FP32-class
+ *                      accuracy). Not for ragged batches.
  *   CORR_PATH_AUTO   : FP32 for CORR_CF32, TENSOR otherwise. */
 typedef enum { CORR_PATH_AUTO = 0, CORR_PATH_FP32 = 1, CORR_PATH_TENSOR = 2 } corr_path_t;
 

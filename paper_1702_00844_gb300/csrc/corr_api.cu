@@ -98,6 +98,10 @@ bool aligned_to(const void *p, uintptr_t a) { return !p || (reinterpret_cast<uin
 
 long long n_baselines(long long S) { return S * (S + 1) / 2; }
 
+// Internal path id of a plan with FP32 samples on the tensor cores (path
+// CORR_PATH_TENSOR, dtype CORR_CF32 in the descriptor).
+constexpr int PATH_TF32 = 3;
+
 int tc_blocks(int S) { return (S + TC_SIDE - 1) / TC_SIDE; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -160,6 +164,31 @@ corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled (input gradient) failed (%d)", (int)r);
+        return CORR_ERR_CUDA;
+    }
+    return CORR_OK;
+}
+
+// The samples for the tf32-split tensor correlator as 8-byte elements (one
+// complex float per pol, copied bit for bit): dims (2T per station, stations,
+// units, 1), boxes of 32 elements (16 samples x 2 pols) x 64 stations: one
+// contiguous 256-byte run per station, landing station-major.
+corr_status_t encode_tf32_map(CUtensorMap *m, const void *d_in, int S, int T, long long units)
+{
+    auto fn = encode_fn();
+    if (!fn) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled unavailable");
+        return CORR_ERR_CUDA;
+    }
+    cuuint64_t dims[4] = {2 * (cuuint64_t)T, (cuuint64_t)S, (cuuint64_t)units, 1};
+    cuuint64_t strides[3] = {(cuuint64_t)T * 16, (cuuint64_t)S * T * 16, (cuuint64_t)units * S * T * 16};
+    cuuint32_t box[4] = {32, 64, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(d_in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled (tf32 correlator) failed (%d)", (int)r);
         return CORR_ERR_CUDA;
     }
     return CORR_OK;
@@ -431,6 +460,25 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
     const corr_desc_t &d = h->d;
     const size_t out_bytes = (size_t)units * out_unit_bytes(d);
     if (d.n_samples == 0) return cuda_status(cudaMemsetAsync(d_out, 0, out_bytes, s));
+    if (h->path == PATH_TF32) {
+        CUtensorMap m{};
+        corr_status_t st = encode_tf32_map(&m, d_in, d.n_stations, d.n_samples, units);
+        if (st != CORR_OK) return st;
+        TfParams p{};
+        p.out = static_cast<float2 *>(d_out);
+        p.S = d.n_stations;
+        p.T = d.n_samples;
+        p.units = (int)units;
+        p.nb = (d.n_stations + 63) / 64;
+        p.chunk_kb = 16;   // 256 samples per accumulator chunk
+        p.err = h->d_err;
+        p.wait_ns = h->wait_ns;
+        const bool mark = h->ev_k0 && h->ev_k1;
+        if (mark) cudaEventRecord(h->ev_k0, s);
+        st = cuda_status(tf32_correlate_launch(&m, p, s));
+        if (mark) cudaEventRecord(h->ev_k1, s);
+        return st;
+    }
     if (h->path == CORR_PATH_FP32) {
         CUtensorMap m{};
         if (d.n_pols == 2) {
@@ -959,7 +1007,11 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
     int path = d.path;
     if (path == CORR_PATH_AUTO) path = d.dtype == CORR_CF32 ? CORR_PATH_FP32 : CORR_PATH_TENSOR;
     if (path == CORR_PATH_FP32 && d.dtype != CORR_CF32) return CORR_ERR_UNSUPPORTED;
-    if (path == CORR_PATH_TENSOR && d.dtype == CORR_CF32) return CORR_ERR_UNSUPPORTED;
+    // FP32 samples on the tensor cores: the tf32-split kernel (two pols)
+    if (path == CORR_PATH_TENSOR && d.dtype == CORR_CF32) {
+        if (d.n_pols != 2) return CORR_ERR_UNSUPPORTED;
+        path = PATH_TF32;
+    }
     if (d.dtype == CORR_CI8 && d.n_samples > 65535) return CORR_ERR_UNSUPPORTED; // int32 range
     const long long units = (long long)d.n_channels * d.n_integrations;
     if (units > (1LL << 30) || d.n_stations > 65535) return CORR_ERR_UNSUPPORTED;
@@ -994,7 +1046,7 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
                 (st = cuda_status(cudaMalloc(&h->d_fp_partial, (size_t)h->fp.ksplit * units *
                                                                    out_unit_bytes(d)))) != CORR_OK)
                 break;
-        } else {
+        } else if (path == CORR_PATH_TENSOR) {
             if ((st = tune_tensor_config(h)) != CORR_OK) break;
             std::vector<int4> tail;
             std::vector<int4> items =
@@ -1021,6 +1073,10 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
             long long cu = (long long)((chunk_mb << 20) / ub);
             if (h->path == CORR_PATH_FP32)
                 cu = std::max<long long>(cu, (2LL * h->sm_count + h->fp.groups - 1) / h->fp.groups);
+            if (h->path == PATH_TF32) {   // a tile per CTA and SM: at least one wave of tiles
+                const long long nb = (d.n_stations + 63) / 64, ntri = nb * (nb + 1) / 2;
+                cu = std::max<long long>(cu, (h->sm_count + ntri - 1) / ntri);
+            }
             h->chunk_units = (int)std::max<long long>(1, std::min<long long>(units, cu));
             const size_t ib = (size_t)h->chunk_units * in_unit_bytes(d);
             const size_t ob = (size_t)h->chunk_units * out_unit_bytes(d);

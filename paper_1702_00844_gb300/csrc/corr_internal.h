@@ -71,6 +71,18 @@ struct IgParams {
 #ifndef CORR_IG_A_FP32
 #define CORR_IG_A_FP32 0
 #endif
+// FP32 samples on the tensor cores (corr_tf32.cu): tf32 value + remainder
+// split, three products, FP32 accumulation; two pols, complex64 samples
+// [unit][S][T][2] read through a TMA map of 8-byte elements.
+struct TfParams {
+    float2 *out;              // [unit][baseline][2][2] complex
+    int S, T, units, nb;      // nb = blocks of 64 stations
+    int chunk_kb;             // K-blocks of 16 samples per accumulator chunk
+    int *err;
+    unsigned long long wait_ns;
+};
+cudaError_t tf32_correlate_launch(const void *xmap, const TfParams &p, cudaStream_t s);
+
 // Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
 __host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
 __host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }

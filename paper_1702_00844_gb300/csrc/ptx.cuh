@@ -470,10 +470,12 @@ __device__ __forceinline__ float tf32_round(float v)
 }
 
 // Instruction descriptor of kind::tf32: A and B tf32 (format 2 in bits 7-9
-// and 10-12), f32 accumulator, both operands K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N)
+// and 10-12), f32 accumulator, both operands K-major, A negated if neg_a
+// (bit 13).
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N, bool neg_a = false)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 } // namespace corr

@@ -148,7 +148,7 @@ def test_create_rejects_bad_descriptions_without_gpu(L):
     unsupported = [Desc(4, 3, 1, 1, 1, 0, 0, 0),   # three polarisations
                    Desc(4, 1, 1, 1, 1, 0, 1, 4 | 1),  # one pol with gain calibration
                    Desc(4, 2, 1, 1, 1, 1, 1, 0),   # FP16 on the FP32 path
-                   Desc(4, 2, 1, 1, 1, 0, 2, 0),   # FP32 on the tensor path
+                   Desc(4, 1, 1, 1, 1, 0, 2, 0),   # FP32 on the tensor path with one pol
                    Desc(4, 2, 1, 70000, 1, 2, 0, 0)]  # int8 with T beyond the INT32 range
     for d in unsupported:
         assert L.corr_create(ctypes.byref(d), ctypes.byref(h)) == 2

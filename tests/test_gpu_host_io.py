@@ -1,6 +1,7 @@
 """corr_correlate_host: host buffers streamed in chunks with the copies
 overlapping the kernels must give exactly what corr_correlate gives on
-device buffers (both kernel paths, several chunks and a ragged last chunk),
+device buffers (every kernel path, FP32 samples on the tensor cores
+included; several chunks and a ragged last chunk),
 and match the FP64 oracle on sampled channels (the first, one in the middle
 and the last, so that the first, a middle and the ragged last chunk are
 covered): bit for bit for int8, within the accumulation tolerances for f16
@@ -16,9 +17,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dtype,S,C,T", [("ci8", 256, 300, 1024), ("cf16", 130, 200, 700),
-                                          ("cf32", 64, 200, 768), ("ci8", 70, 3, 0)])
-def test_host_streaming_equals_device_call(dtype, S, C, T):
+@pytest.mark.parametrize("dtype,S,C,T,path", [("ci8", 256, 300, 1024, "auto"), ("cf16", 130, 200, 700, "auto"),
+                                               ("cf32", 64, 200, 768, "auto"), ("ci8", 70, 3, 0, "auto"),
+                                               ("cf32", 64, 200, 768, "tensor")])
+def test_host_streaming_equals_device_call(dtype, S, C, T, path):
     from paper_1702_00844_gb300 import FLAG_HOST_IO, Plan
     g = synth.rng(90, S + C)
     if dtype == "ci8":
@@ -27,7 +29,7 @@ def test_host_streaming_equals_device_call(dtype, S, C, T):
         x = torch.from_numpy(synth.to_cf16(synth.complex_normal(g, (C, S, T, 2))))
     else:
         x = torch.from_numpy(synth.complex_normal(g, (C, S, T, 2)))
-    plan = Plan(S, C, T, dtype=dtype, flags=FLAG_HOST_IO)
+    plan = Plan(S, C, T, dtype=dtype, path=path, flags=FLAG_HOST_IO)
     xh = x.contiguous().pin_memory()
     oh = plan.empty_out("cpu").pin_memory()
     plan.correlate_host(xh, oh)
