@@ -13,10 +13,11 @@
 // correlator's op count.
 //
 // tcgen05 has no FP32 MMA. Every operand value is split into hi = the value
-// rounded to tf32 and lo = (value - hi), exact in FP32, rounded to tf32, and
-// each product above is A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32, FP32
-// accumulation in TMEM; the dropped A_lo B_lo and lo's rounding are about
-// 2^-22 of each product): three MMAs per product, 24 per K-block.
+// rounded to tf32 and lo = (value - hi), exact in FP32, of which the MMA
+// uses the tf32 bits, and each product above is A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (kind::tf32, FP32 accumulation in TMEM; the dropped A_lo B_lo
+// and lo's lost bits are at most about 2^-21 of each product): three MMAs
+// per product, 24 per K-block.
 //
 // The tensor core adds each MMA's result to the FP32 accumulator with an
 // error of about half an ulp of the running sum, biased toward zero, so a
@@ -37,7 +38,7 @@
 //     each lands station-major in its operand's lo tile;
 //   - TF_SW warps read the raw samples (a pair of stations per warp and
 //     iteration, conflict-free), meet on an mbarrier, transpose each quad of
-//     lanes' 4 times x (X re, X im, Y re, Y im) with shuffles, and write hi
+//     lanes' 4 times x (X re, X im, Y re, Y im) in two shuffle rounds, and write hi
 //     and lo chunks into the 128-byte swizzled K-major rows (chunk q of row
 //     r at q ^ (r mod 8));
 //   - one thread issues the 24 MMAs;
@@ -55,7 +56,7 @@ namespace corr {
 namespace {
 
 #ifndef CORR_TF_SPLIT_WARPS
-#define CORR_TF_SPLIT_WARPS 16
+#define CORR_TF_SPLIT_WARPS 8
 #endif
 // warp 0 loads, warps 1 .. SW split, the next four store (each a different
 // TMEM lane quarter, warp % 4), the last allocates TMEM and issues the MMAs
@@ -104,11 +105,6 @@ __device__ __forceinline__ TfTile tf_tile(long long tile, const TfParams &p)
     r.cb = cb;
     r.rb = k;
     return r;
-}
-
-__device__ __forceinline__ uint32_t sel4(const uint4 &v, int i)
-{
-    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
 __global__ void __launch_bounds__(TF_THREADS, 1)
@@ -193,7 +189,6 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     } else if (warp <= TF_SW) {
         // ------------------------------------------------------------ split
         const int j = lane & 3;              // this lane's component after the transpose
-        const int qbase = lane & ~3;
         long long g = 0;
         bool ok = true;
         for (int i = 0; i < my_tiles && ok; ++i) {
@@ -238,26 +233,34 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                         const uint32_t hi = o == 0 ? a_hi(s) : b_hi(s), lo = o == 0 ? a_lo(s) : b_lo(s);
 #pragma unroll
                         for (int q = 0; q < NE; ++q) {
-                            // 4 x 4 transpose within the quad: lane j ends with
-                            // component j of the quad's four times
-                            float out[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const int src = (j + r) & 3;
-                                const uint32_t send = sel4(v[o][q], (j - r) & 3);
-                                const float got = __uint_as_float(__shfl_sync(0xffffffffu, send, qbase + src));
-#pragma unroll
-                                for (int mm = 0; mm < 4; ++mm) out[mm] = mm == src ? got : out[mm];
-                            }
+                            // 4 x 4 transpose within the quad (lane j: time j,
+                            // components c0..c3) in two exchange rounds: with
+                            // the partner across bit 0 keep components of
+                            // parity j & 1 for both times of the pair, then with
+                            // the partner across bit 1 keep component j for all
+                            // four times
+                            const uint4 c = v[o][q];
+                            const bool b0 = (j & 1) != 0, b1 = (j & 2) != 0;
+                            const uint32_t r0 = __shfl_xor_sync(0xffffffffu, b0 ? c.x : c.y, 1);
+                            const uint32_t r1 = __shfl_xor_sync(0xffffffffu, b0 ? c.z : c.w, 1);
+                            const uint32_t u0 = b0 ? r0 : c.x, u1 = b0 ? c.y : r0;
+                            const uint32_t u2 = b0 ? r1 : c.z, u3 = b0 ? c.w : r1;
+                            const uint32_t q0 = __shfl_xor_sync(0xffffffffu, b1 ? u0 : u2, 2);
+                            const uint32_t q1 = __shfl_xor_sync(0xffffffffu, b1 ? u1 : u3, 2);
+                            const float out[4] = {__uint_as_float(b1 ? q0 : u0), __uint_as_float(b1 ? q1 : u1),
+                                                  __uint_as_float(b1 ? u2 : q0), __uint_as_float(b1 ? u3 : q1)};
                             const int st = 2 * (q * TF_SW + w) + st_off;
                             const int row = 2 * st + (j >> 1);
                             const int chunk = (j & 1) * 4 + tq;
                             const uint32_t sw = (uint32_t)(row * 128 + ((chunk ^ (row & 7)) * 16));
+                            // hi = the tf32 rounding; lo = the exact remainder,
+                            // whose bits below tf32 the MMA does not use (an
+                            // error of at most 2^-21 of the value)
                             float hv[4], lv[4];
 #pragma unroll
                             for (int mm = 0; mm < 4; ++mm) {
                                 hv[mm] = tf32_round(out[mm]);
-                                lv[mm] = tf32_round(out[mm] - hv[mm]);
+                                lv[mm] = out[mm] - hv[mm];
                             }
                             sts128(hi + sw, make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]),
                                                        __float_as_uint(hv[2]), __float_as_uint(hv[3])));
