@@ -339,7 +339,23 @@ def oracle_errors(torch):
     res["differentiation_fp32"] = {"channels": [0, 31, 63], "loss_rel": abs(float(loss) - Lref) / Lref,
                                    "grad_gain_max_rel": eg, "grad_samples_max_rel": ex,
                                    "bound": "1e-4 (gradients)"}
-    del pg
+    # the same with the forward correlation on the tensor cores (tf32 split)
+    pt = Plan(d["S"], d["C"], d["T"], dtype="cf32", path="tensor", flags=FLAG_GAINS)
+    Rt = pt.correlate(xd)
+    gg, gx = pt.gain_backward(xd, gd, Md, R=Rt, loss=loss)
+    torch.cuda.synchronize()
+    gg, gx = gg.cpu().numpy(), gx.cpu().numpy()
+    eg, ex = 0.0, 0.0
+    for c in (0, 31, 63):
+        Rc = oracle.correlate(d["x"][c][None])
+        gr = oracle.gain_grad(Rc, d["g"][c][None], d["M"][c][None])
+        xr = oracle.input_grad(d["x"][c][None], Rc, d["g"][c][None], d["M"][c][None])
+        eg = max(eg, float(np.abs(gg[c][None] - gr).max() / np.abs(gr).max()))
+        ex = max(ex, float(np.abs(gx[c][None] - xr).max() / np.abs(xr).max()))
+    res["differentiation_tf32_forward"] = {"channels": [0, 31, 63], "loss_rel": abs(float(loss) - Lref) / Lref,
+                                           "grad_gain_max_rel": eg, "grad_samples_max_rel": ex,
+                                           "bound": "1e-4 (gradients)"}
+    del pg, pt
     torch.cuda.empty_cache()
     return res
 
@@ -566,8 +582,18 @@ def secondary(x8, torch):
         pg.gain_backward(xd, gd, Md, R=R)
 
     ms = time_launches(step, 10, 3, st)
-    res["gain_forward_backward_differentiation"] = {"ms": ms}
-    del pg, xd, gd, Md, R, gg, gx
+    res["gain_forward_backward_differentiation"] = {"ms": ms, "forward": "FP32 CUDA cores"}
+    # the same step with the forward correlation on the tensor cores (tf32
+    # value + remainder split)
+    pt = Plan(d["S"], d["C"], d["T"], dtype="cf32", path="tensor", flags=FLAG_GAINS)
+
+    def step_t():
+        pt.correlate(xd, R)
+        pt.gain_backward(xd, gd, Md, R=R)
+
+    ms = time_launches(step_t, 10, 3, st)
+    res["gain_forward_backward_differentiation_tf32_forward"] = {"ms": ms, "forward": "tensor cores, tf32 split"}
+    del pg, pt, xd, gd, Md, R, gg, gx
     torch.cuda.empty_cache()
     # one polarisation: the int8 samples read as 512 stations of one pol (the
     # same bytes, and the same products per channel as 256 two-pol stations)

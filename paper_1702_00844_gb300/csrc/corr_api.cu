@@ -83,6 +83,8 @@ struct corr_plan {
     float2 *d_R = nullptr;     // recomputed raw visibilities
     float2 *d_W = nullptr;     // W' per channel
     float *d_At = nullptr;     // W' as the tensor-core input gradient's A' tiles
+    // FP32 samples on the tensor cores with few tiles: per-chunk partial sums
+    float2 *d_tf_partial = nullptr;
     float *d_partial = nullptr;
 };
 
@@ -101,6 +103,10 @@ long long n_baselines(long long S) { return S * (S + 1) / 2; }
 // Internal path id of a plan with FP32 samples on the tensor cores (path
 // CORR_PATH_TENSOR, dtype CORR_CF32 in the descriptor).
 constexpr int PATH_TF32 = 3;
+constexpr int TF_CHUNK_KB = 16;   // 256 samples per accumulator chunk
+
+// Accumulator chunks of a tf32-split tile over T samples.
+long long tf_chunks(int T) { return ((T + 15) / 16 + TF_CHUNK_KB - 1) / TF_CHUNK_KB; }
 
 int tc_blocks(int S) { return (S + TC_SIDE - 1) / TC_SIDE; }
 
@@ -122,6 +128,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 // FP32 input as a 4-D tensor: (4 floats of one station and time) x station x
 // time x unit, boxes of 4 x 8 stations x tc samples x 1 unit, so that a box
 // lands in shared memory as [t][8 stations][4 floats].
+// With fewer tiles than two per SM, tf32-split plans spread the chunks of
+// each tile over the CTAs (partial sums summed afterwards).
+bool tf_use_partial(const corr_plan *h, long long units)
+{
+    const long long nb = (h->d.n_stations + 63) / 64, ntri = nb * (nb + 1) / 2;
+    return h->d_tf_partial && tf_chunks(h->d.n_samples) > 1 && units * ntri < 2LL * h->sm_count;
+}
+
 corr_status_t encode_fp32_map(CUtensorMap *m, const void *d_in, int S, int T, int units, int tc)
 {
     auto fn = encode_fn();
@@ -470,7 +484,10 @@ corr_status_t launch_units(corr_plan *h, const void *d_in, void *d_out, long lon
         p.T = d.n_samples;
         p.units = (int)units;
         p.nb = (d.n_stations + 63) / 64;
-        p.chunk_kb = 16;   // 256 samples per accumulator chunk
+        p.chunk_kb = TF_CHUNK_KB;
+        // fewer tiles than two per SM: every chunk of a tile is a work item
+        // of its own, summed by a second kernel
+        p.partial = tf_use_partial(h, units) ? h->d_tf_partial : nullptr;
         p.err = h->d_err;
         p.wait_ns = h->wait_ns;
         const bool mark = h->ev_k0 && h->ev_k1;
@@ -1046,6 +1063,12 @@ corr_status_t corr_create(const corr_desc_t *desc, corr_handle_t *out)
                 (st = cuda_status(cudaMalloc(&h->d_fp_partial, (size_t)h->fp.ksplit * units *
                                                                    out_unit_bytes(d)))) != CORR_OK)
                 break;
+        } else if (path == PATH_TF32) {
+            const long long nb = (d.n_stations + 63) / 64, ntri = nb * (nb + 1) / 2;
+            if (tf_chunks(d.n_samples) > 1 && units * ntri < 2LL * h->sm_count &&
+                (st = cuda_status(cudaMalloc(&h->d_tf_partial, (size_t)tf_chunks(d.n_samples) * units *
+                                                                   out_unit_bytes(d)))) != CORR_OK)
+                break;
         } else if (path == CORR_PATH_TENSOR) {
             if ((st = tune_tensor_config(h)) != CORR_OK) break;
             std::vector<int4> tail;
@@ -1531,6 +1554,7 @@ corr_status_t corr_destroy(corr_handle_t h)
     cudaFree(h->d_R);
     cudaFree(h->d_W);
     cudaFree(h->d_At);
+    cudaFree(h->d_tf_partial);
     cudaFree(h->d_partial);
     delete h;
     return CORR_OK;

@@ -78,6 +78,9 @@ struct TfParams {
     float2 *out;              // [unit][baseline][2][2] complex
     int S, T, units, nb;      // nb = blocks of 64 stations
     int chunk_kb;             // K-blocks of 16 samples per accumulator chunk
+    // nullable: with few tiles, each chunk of a tile is its own work item
+    // writing partial[chunk][unit][baseline][2][2], summed afterwards
+    float2 *partial;
     int *err;
     unsigned long long wait_ns;
 };

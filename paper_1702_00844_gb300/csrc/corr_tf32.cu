@@ -88,14 +88,24 @@ static_assert(tf_smem_bytes() <= 227 * 1024, "tf32 correlator stages must fit in
 
 struct TfTile {
     int unit, rb, cb;
+    int c0, c1;   // the item's accumulator chunks [c0, c1)
 };
 
-// Tile `tile` of the flattened (unit, column block, row block <= column
-// block) space.
-__device__ __forceinline__ TfTile tf_tile(long long tile, const TfParams &p)
+// Work item `item`: a tile of the flattened (unit, column block, row block
+// <= column block) space with all its chunks, or (with p.partial) one chunk
+// of a tile.
+__device__ __forceinline__ TfTile tf_tile(long long item, int nch, const TfParams &p)
 {
     const int ntri = p.nb * (p.nb + 1) / 2;
     TfTile r;
+    long long tile = item;
+    r.c0 = 0;
+    r.c1 = nch;
+    if (p.partial) {
+        tile = item / nch;
+        r.c0 = (int)(item % nch);
+        r.c1 = r.c0 + 1;
+    }
     r.unit = (int)(tile / ntri);
     int k = (int)(tile % ntri), cb = 0;
     while (k > cb) {
@@ -119,8 +129,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KB = (p.T + TF_KT - 1) / TF_KT;
     const int nch = (KB + p.chunk_kb - 1) / p.chunk_kb;   // accumulator chunks per tile
-    const long long n_tiles = (long long)p.units * (p.nb * (p.nb + 1) / 2);
-    const int my_tiles = (int)((n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    const long long n_items = (long long)p.units * (p.nb * (p.nb + 1) / 2) * (p.partial ? nch : 1);
+    const int my_tiles = (int)((n_items - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
     if (tid == 0) {
         prefetch_tmap(&xmap);
@@ -157,9 +167,10 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             long long g = 0;   // K blocks issued so far (over all tiles)
             bool ok = true;
             for (int i = 0; i < my_tiles && ok; ++i) {
-                const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, p);
+                const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, nch, p);
                 const bool diag = tl.rb == tl.cb;
-                for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int kb1 = min(KB, tl.c1 * p.chunk_kb);
+                for (int kb = tl.c0 * p.chunk_kb; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % TF_STAGES);
                     if (g >= TF_STAGES && !mbar_wait_bounded(&bars->empty[s], (uint32_t)((g / TF_STAGES) - 1) & 1,
                                                              abort_flag, p.err, p.wait_ns)) {
@@ -192,9 +203,10 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
         long long g = 0;
         bool ok = true;
         for (int i = 0; i < my_tiles && ok; ++i) {
-            const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, p);
+            const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, nch, p);
             const int nops = tl.rb == tl.cb ? 1 : 2;
-            for (int kb = 0; kb < KB; ++kb, ++g) {
+            const int kb1 = min(KB, tl.c1 * p.chunk_kb);
+            for (int kb = tl.c0 * p.chunk_kb; kb < kb1; ++kb, ++g) {
                 const int s = (int)(g % TF_STAGES);
                 if (!mbar_wait_bounded(&bars->raw[s], (uint32_t)(g / TF_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
                     ok = false;
@@ -285,11 +297,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
         uint32_t it = 0;   // accumulator items (tile chunks) so far
         bool ok = true;
         for (int i = 0; i < my_tiles && ok; ++i) {
-            const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, p);
+            const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, nch, p);
             const int r = quarter * 32 + lane;
             const int s1 = tl.rb * TF_RS + r / 2, p1 = r & 1;
-            float2 *out_u = p.out + (size_t)tl.unit * B * 4;
-            for (int c = 0; c < nch; ++c, ++it) {
+            for (int c = tl.c0; c < tl.c1; ++c, ++it) {
+                // with partials, chunk c of every unit goes to its own copy
+                // of the output (summed by tf32_reduce_kernel)
+                float2 *out_u = (p.partial ? p.partial + (size_t)c * p.units * B * 4 : p.out) +
+                                (size_t)tl.unit * B * 4;
+                const bool add = !p.partial && c > 0;
                 const uint32_t b = it & 1;
                 // the warp leaves together (the TMEM loads below are warp-wide)
                 const bool got =
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                             float4 *dst = reinterpret_cast<float4 *>(out_u + bl * 4 + p1 * 2);
                             float4 v = make_float4(__uint_as_float(re[2 * k]), __uint_as_float(im[2 * k]),
                                                    __uint_as_float(re[2 * k + 1]), __uint_as_float(im[2 * k + 1]));
-                            if (c > 0) {
+                            if (add) {
                                 const float4 o = *dst;
                                 v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
                             }
@@ -339,9 +355,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             for (int i = 0; i < my_tiles && ok; ++i) {
-                const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, p);
+                const TfTile tl = tf_tile(blockIdx.x + (long long)i * gridDim.x, nch, p);
                 const bool diag = tl.rb == tl.cb;
-                for (int c = 0; c < nch && ok; ++c, ++it) {
+                for (int c = tl.c0; c < tl.c1 && ok; ++c, ++it) {
                     const uint32_t b = it & 1;
                     if (it >= 2 && !mbar_wait_bounded(&bars->acc_empty[b], ((it >> 1) - 1) & 1, abort_flag, p.err,
                                                       p.wait_ns)) {
@@ -400,6 +416,20 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     }
 }
 
+// out[i] = sum over the chunks c of partial[c][i], in the order of c (a
+// fixed order: the result does not depend on the launch).
+__global__ void __launch_bounds__(256) tf32_reduce_kernel(const float4 *partial, float4 *out, long long n, int nch)
+{
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        float4 a = partial[i];
+        for (int c = 1; c < nch; ++c) {
+            const float4 b = partial[(size_t)c * n + i];
+            a = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+        }
+        out[i] = a;
+    }
+}
+
 } // namespace
 
 cudaError_t tf32_correlate_launch(const void *xmap, const TfParams &p, cudaStream_t s)
@@ -412,9 +442,17 @@ cudaError_t tf32_correlate_launch(const void *xmap, const TfParams &p, cudaStrea
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const long long n_tiles = (long long)p.units * (p.nb * (p.nb + 1) / 2);
-    const unsigned grid = (unsigned)std::min<long long>(n_tiles, std::max(1, sms));
+    const int KB = (p.T + TF_KT - 1) / TF_KT, nch = (KB + p.chunk_kb - 1) / p.chunk_kb;
+    const long long n_items = (long long)p.units * (p.nb * (p.nb + 1) / 2) * (p.partial ? nch : 1);
+    const unsigned grid = (unsigned)std::min<long long>(n_items, std::max(1, sms));
     tf32_correlate_kernel<<<grid, TF_THREADS, smem, s>>>(*static_cast<const CUtensorMap *>(xmap), p);
+    if ((e = cudaGetLastError()) != cudaSuccess || !p.partial) return e;
+    // the chunks' partial sums, in chunk order
+    const long long n = (long long)p.units * p.S * (p.S + 1) / 2;   // float4 per baseline (2 x 2 complex / 2)
+    const long long n4 = n * 2;
+    const unsigned rg = (unsigned)std::min<long long>((n4 + 255) / 256, 8LL * std::max(1, sms));
+    tf32_reduce_kernel<<<rg, 256, 0, s>>>(reinterpret_cast<const float4 *>(p.partial),
+                                          reinterpret_cast<float4 *>(p.out), n4, nch);
     return cudaGetLastError();
 }
 

@@ -4,8 +4,9 @@ product term, FP32 accumulation. Checked against the FP64 oracle with the
 FP32 path's tolerance (per-channel relative Frobenius error below 1e-5) and
 element-wise through the correlation-coefficient error, on shapes that
 span several 64-station blocks with a partial last one, sample counts that
-are not multiples of the 16-sample K-block, diagonal-only problems, and the
-production workload (sampled channels)."""
+are not multiples of the 16-sample K-block, diagonal-only problems, both
+ways of summing 256-sample accumulator chunks, and the production workload
+(sampled channels)."""
 import numpy as np
 import pytest
 
@@ -40,6 +41,22 @@ def test_tf32_split_correlator_vs_oracle(S, C, T):
     assert np.isfinite(got).all()
     assert rel_frobenius_per_unit(got, ref).max() < 1e-5
     assert coef_error(got, ref, S) < 1e-5
+
+
+def test_tf32_split_correlator_both_chunk_modes():
+    """More samples than one 256-sample accumulator chunk, with many tiles
+    (320 channels: chunks summed by the epilogue into the output) and with
+    few (4 channels: every chunk a work item of its own, partial sums added
+    by a second kernel); sampled channels against the oracle."""
+    S, T = 64, 600
+    for C in (320, 4):
+        g = synth.rng(140 + C)
+        x = synth.complex_normal(g, (C, S, T, 2))
+        got = _run(x, S, C, T)
+        for c in sorted({0, C // 2, C - 1}):
+            ref = oracle.correlate(x[c][None])
+            assert rel_frobenius_per_unit(got[c][None], ref).max() < 1e-5, C
+            assert coef_error(got[c][None], ref, S) < 1e-5, C
 
 
 def test_tf32_split_correlator_integrations_and_exact_integers():
