@@ -12,10 +12,11 @@
 //
 // FP32 accuracy from tf32 tensor cores (tcgen05 kind::tf32): every operand
 // is split into hi = its value rounded to tf32 (11 significant bits) and
-// lo = (value - hi), exact in FP32, rounded to tf32 as well, and
+// lo = (value - hi), exact in FP32 (rounded to tf32 for A', by the
+// gain-gradient kernel; for the samples the MMA uses its tf32 bits), and
 //     A'B' ~ A_hi B_hi + A_hi B_lo + A_lo B_hi
-// accumulated in FP32 (the dropped A_lo B_lo and lo's rounding are about
-// 2^-22 of each product).
+// accumulated in FP32 (the dropped A_lo B_lo and lo's lost bits are at most
+// about 2^-21 of each product).
 //
 // Tiles of (channel, 128-row tile of M', IG_N-time tile of N), spread over
 // one persistent CTA per SM; or, with two row tiles or more, tiles of two
@@ -272,9 +273,9 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                         make_float4(tf32_round(f.x), tf32_round(f.y), tf32_round(f.z), tf32_round(f.w));
                     const uint4 h = make_uint4(__float_as_uint(hf.x), __float_as_uint(hf.y), __float_as_uint(hf.z),
                                                __float_as_uint(hf.w));
-                    const uint4 l = make_uint4(
-                        __float_as_uint(tf32_round(f.x - hf.x)), __float_as_uint(tf32_round(f.y - hf.y)),
-                        __float_as_uint(tf32_round(f.z - hf.z)), __float_as_uint(tf32_round(f.w - hf.w)));
+                    // lo: the exact remainder, of which the MMA uses the tf32 bits
+                    const uint4 l = make_uint4(__float_as_uint(f.x - hf.x), __float_as_uint(f.y - hf.y),
+                                               __float_as_uint(f.z - hf.z), __float_as_uint(f.w - hf.w));
                     const uint32_t sw = (uint32_t)(t * 128 + ((st ^ (t & 7)) * 16));
                     sts128(b_hi(s) + sw, h);
                     sts128(b_lo(s) + sw, l);
