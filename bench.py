@@ -735,11 +735,32 @@ def run_ours(args):
     e2e_ms = time_launches(lambda: plan_io.correlate_host(xh, oh), e2e_steps, 1, stream)
     plan_io.check_error()
     e2e_val, e2e_ms, _ = job_throughput(ops, e2e_ms, 1, device="cuda")
+    # the host link's own bound for this step (Section 3.6's perf_max with
+    # the link as the bandwidth): the same bytes copied both ways at once,
+    # H2D and D2H on two streams, no kernel
+    xd_, od_ = torch.empty_like(xh, device="cuda"), torch.empty_like(oh, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def copies():
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        with torch.cuda.stream(s_in):
+            xd_.copy_(xh, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            oh.copy_(od_, non_blocking=True)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+
+    link_ms = time_launches(copies, e2e_steps, 1, stream)
+    link_ms = max_over_ranks(link_ms, device="cuda")
     e2e = {"value": e2e_val, "unit": UNIT,
            "h2d_bytes_per_step": xh.numel() * xh.element_size(),
            "d2h_bytes_per_step": oh.numel() * oh.element_size(), "ms_per_step": e2e_ms,
-           "api": "corr_correlate_host (chunked, copies overlapped with kernels)"}
-    del xh, oh, plan_io
+           "api": "corr_correlate_host (chunked, copies overlapped with kernels)",
+           "link_only_ms": link_ms,
+           "link_bound_TOPS": ops / (link_ms * 1e-3) / 1e12,
+           "frac_of_link_bound": link_ms / e2e_ms}
+    del xh, oh, plan_io, xd_, od_
 
     peaks, peak_src = measured_peaks()
     in_bps = {"s8": 4, "f16": 8, "f32": 16}[dtype_label]
