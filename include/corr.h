@@ -216,7 +216,7 @@ corr_status_t corr_reorder(int n_stations, int n_channels, int n_samples, int n_
 
 /* Tile variant the plan's tensor path uses: 0 = 64x64-station tiles,
  * 1 = 64 x up to 128 stations, 2 = 128x128-station tiles on a cluster of two
- * CTAs (CTA-pair MMAs); -1 for FP32 plans or NULL. Chosen in corr_create by
+ * CTAs (CTA-pair MMAs); -1 for FP32 samples (either path) or NULL. Chosen in corr_create by
  * timing each (see CORR_FLAG_NO_AUTOTUNE); the environment variable
  * CORR_TC_VARIANT=narrow|wide|pair forces one (pair falls back to wide where
  * a cluster of two such CTAs cannot be resident). */
@@ -227,7 +227,9 @@ int corr_tile_variant(corr_handle_t h);
  * ev_start on its stream right before the launch of the plan's main kernel
  * (tensor path: the first launch over its main tile list, i.e. the
  * power-checked launch of int8, not the redo or tail launches; FP32 path:
- * the correlation kernel and, for a split sample axis, its reduction) and
+ * the correlation kernel and, for a split sample axis, its reduction; FP32
+ * samples on the tensor cores: the correlation kernel and its chunk
+ * reduction) and
  * ev_stop right after it, so cudaEventElapsedTime gives that kernel's
  * duration. The plan does not own the events; NULL, NULL turns the hook off.
  * CORR_ERR_INVALID_ARG if only one is NULL. */
@@ -249,7 +251,7 @@ int corr_batch_tile_variant(corr_handle_t h);
  * process, 4 read from the tuning cache file (CORR_TUNE_CACHE, "off" for
  * none; default $XDG_CACHE_HOME/corr_gb300/tune.txt or
  * ~/.cache/corr_gb300/tune.txt; lines of other library builds are ignored).
- * Any output may be NULL. CORR_ERR_INVALID_ARG for a FP32-path plan. */
+ * Any output may be NULL. CORR_ERR_INVALID_ARG for a plan of FP32 samples. */
 corr_status_t corr_tile_config(corr_handle_t h, int *variant, int *tail, int *layout, int *source);
 
 /* The candidates the autotuner timed (batch = 0: in corr_create; 1: for the
