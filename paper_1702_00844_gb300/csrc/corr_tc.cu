@@ -489,12 +489,17 @@ __device__ __forceinline__ int n_chunks(int nkb, int chunk_kb)
 // Stores the visibilities of one TMEM column group: row (s1, p1) of this
 // thread against column stations s2_0 .. s2_0+7 (both p2), masked to
 // s1 <= s2 < S. int8: converts the exact FP32 chunk sums to INT32 and adds
-// the earlier chunks' partial sums (fold).
-template <int DT, int NPOL>
-__device__ __forceinline__ void store_group(const TcProblem &P, long long unit_off, int s1, int s2_0,
-                                            bool fold, bool last, const uint32_t (&vre)[16],
-                                            const uint32_t (&vim)[16])
+// the earlier chunks' partial sums (fold). PLAIN: the common case, one chunk
+// (no fold, streaming stores), with the branches of the others compiled out:
+// the epilogue issues these stores while the accumulator is held, one warp
+// per scheduler, so every instruction counts.
+template <int DT, int NPOL, bool PLAIN>
+__device__ __forceinline__ void store_group_impl(const TcProblem &P, long long unit_off, int s1, int s2_0,
+                                                 bool fold_arg, bool last_arg, const uint32_t (&vre)[16],
+                                                 const uint32_t (&vim)[16])
 {
+    const bool fold = !PLAIN && fold_arg;
+    const bool last = PLAIN || last_arg;
     if constexpr (NPOL == 1) {
         // s1: this row's station; column k = 2j + p2 is station s2b + k with
         // s2b = 2 s2_0; one complex per baseline. Twice the stores of the
@@ -528,17 +533,30 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
         }
         return;
     }
+    // Two pols: baseline tri(s2_0 + j) + s1 = tri(s2_0) + s1 + j*s2_0 +
+    // j(j+1)/2, 4 complex values each; one multiply-add per store from the
+    // group's first index.
+    const long long base = unit_off + ((long long)s2_0 * (s2_0 + 1) / 2 + s1) * 4;
+    const int lo = s1 - s2_0, hi = P.S - s2_0;   // valid columns: lo <= j < hi
     if (DT == 1) {
-        float2 *out = static_cast<float2 *>(P.out) + unit_off;
+        float2 *out = static_cast<float2 *>(P.out) + base;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int s2 = s2_0 + j;
-            if (s1 <= s2 && s2 < P.S) {
-                const float4 v = make_float4(__uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
-                                             __uint_as_float(vre[2 * j + 1]),
-                                             __uint_as_float(vim[2 * j + 1]));
-                st_global_cs(out + ((long long)s2 * (s2 + 1) / 2 + s1) * 4, v);
-            }
+            if (j < lo || j >= hi) continue;
+            const float4 v = make_float4(__uint_as_float(vre[2 * j]), __uint_as_float(vim[2 * j]),
+                                         __uint_as_float(vre[2 * j + 1]), __uint_as_float(vim[2 * j + 1]));
+            st_global_cs(out + (j * s2_0 + j * (j + 1) / 2) * 4, v);
+        }
+    } else if (PLAIN) {
+        int2 *out = static_cast<int2 *>(P.out) + base;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < lo || j >= hi) continue;
+            const int4 v = make_int4(__float2int_rn(__uint_as_float(vre[2 * j])),
+                                     __float2int_rn(__uint_as_float(vim[2 * j])),
+                                     __float2int_rn(__uint_as_float(vre[2 * j + 1])),
+                                     __float2int_rn(__uint_as_float(vim[2 * j + 1])));
+            st_global_cs(out + (j * s2_0 + j * (j + 1) / 2) * 4, v);
         }
     } else {
         int2 *out = static_cast<int2 *>(P.out) + unit_off;
@@ -571,6 +589,17 @@ __device__ __forceinline__ void store_group(const TcProblem &P, long long unit_o
             }
         }
     }
+}
+
+template <int DT, int NPOL>
+__device__ __forceinline__ void store_group(const TcProblem &P, long long unit_off, int s1, int s2_0,
+                                            bool fold, bool last, const uint32_t (&vre)[16],
+                                            const uint32_t (&vim)[16])
+{
+    if (DT == 1 || (!fold && last))
+        store_group_impl<DT, NPOL, true>(P, unit_off, s1, s2_0, false, true, vre, vim);
+    else
+        store_group_impl<DT, NPOL, false>(P, unit_off, s1, s2_0, fold, last, vre, vim);
 }
 
 // NPOL = 2: rows are (station, pol). NPOL = 1: rows are stations; stations
