@@ -549,9 +549,10 @@ __device__ __forceinline__ void store_group_impl(const TcProblem &P, long long u
         }
     } else if (PLAIN) {
         int2 *out = static_cast<int2 *>(P.out) + base;
+        const bool all = lo <= 0 && hi >= 8;   // the whole group lies in the triangle
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            if (j < lo || j >= hi) continue;
+            if (!all && (j < lo || j >= hi)) continue;
             const int4 v = make_int4(__float2int_rn(__uint_as_float(vre[2 * j])),
                                      __float2int_rn(__uint_as_float(vim[2 * j])),
                                      __float2int_rn(__uint_as_float(vre[2 * j + 1])),
