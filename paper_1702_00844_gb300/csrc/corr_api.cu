@@ -411,10 +411,14 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int lay
     // measurement hook (corr_set_kernel_events): around the main list's
     // first launch only
     const bool mark = ctr == 0 && h->ev_k0 && h->ev_k1;
-    // The tail list (ctr 1) reads nothing the main list's launches write:
-    // its first launch is a programmatic dependent that needs no wait, so
-    // its CTAs take SMs as soon as the main launch's CTAs leave them.
-    const bool pdl = ctr == 1;
+    // Both lists' first launches are programmatic dependents, so that their
+    // CTAs take SMs as soon as the previous kernel's CTAs leave them. The
+    // main list (ctr 0) may read what the kernel before it wrote: its CTAs
+    // wait for that kernel after their set-up (dep_wait). The tail list
+    // (ctr 1) reads nothing the main list's launches write and needs no
+    // wait.
+    const bool pdl = true;
+    p.dep_wait = ctr == 0 ? 1 : 0;
     if (!checked) {
         p.chunk_kb = dtype == CORR_CI8 ? TC_INT8_CHUNK_KB : 0;
         if (mark) cudaEventRecord(h->ev_k0, s);
@@ -448,6 +452,7 @@ corr_status_t run_list(corr_plan *h, TcParams p, int dtype, int variant, int lay
     b.chunk_kb = TC_INT8_CHUNK_KB;
     b.check_power = 0;
     b.redo_done = count + 1;
+    b.dep_wait = 0;                 // it waits for the checked launch at its start
     return cuda_status(
         tc_launch(dtype, variant, h->d.n_pols, b, tc_grid_for(h, variant, p.n_items), s, true, layout));
 }

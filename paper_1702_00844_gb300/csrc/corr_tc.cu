@@ -633,9 +633,12 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
     const int warp = tid >> 5;
     const int lane = tid & 31;
     // The redo launch reads the count that the launch before it wrote: wait
-    // for that launch's end. Any launch lets its own dependent be scheduled.
+    // for that launch's end. A launch lets its own dependent be scheduled
+    // once it has waited for its own predecessor (a main launch: after its
+    // set-up, below), so that a dependent which does not wait (a tail list)
+    // never starts before what preceded the call on the stream has ended.
     if (p.n_items_dev) griddep_wait();
-    griddep_launch_dependents();
+    if (!p.dep_wait) griddep_launch_dependents();
     const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
     // A pair (cluster of 2 CTAs) shares each work item; rank 0 issues the MMAs.
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
@@ -679,6 +682,13 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
     if constexpr (PAIR) cluster_sync(); // both CTAs' barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem_base = bars->tmem_base;
+    // A main launch scheduled early (programmatic dependent): the set-up
+    // above overlapped the previous kernel's end; its samples and outputs
+    // may be that kernel's, so wait for it here.
+    if (p.dep_wait) {
+        griddep_wait();
+        griddep_launch_dependents();
+    }
 
     if (warp < N_PROD_WARPS) {
         // ------------------------------------------------------ producers

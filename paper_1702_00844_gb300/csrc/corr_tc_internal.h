@@ -40,6 +40,10 @@ struct TcParams {
     int *redo_done;           // redo launch only: CTAs finished (the last one resets the list)
     int *err;                 // device error word
     unsigned long long wait_ns;
+    // launched as a programmatic dependent of whatever kernel precedes it on
+    // the stream: every CTA sets up its barriers and TMEM, then waits for
+    // that kernel's completion before it touches global memory
+    int dep_wait;
 };
 
 // Tile variants of the tensor kernel: narrow = 64x64-station tiles (N=128,
@@ -57,8 +61,11 @@ constexpr int TC_INT8_CHUNK_KB = 16; // 512 samples: |partial| <= 2^24
 // grid: CTAs (even for TC_PAIR: two per cluster). npol: 1 or 2 polarisations
 // (with 1, the items are over pseudo-stations of two stations each).
 // pdl: launched as a programmatic dependent of the previous kernel on the
-// stream (the redo launch; the kernel waits for that kernel's completion
-// before it reads the redo count).
+// stream: the redo launch (the kernel waits for that kernel's completion
+// before it reads the redo count), a main launch with dep_wait set (it waits
+// after its set-up), or a tail list (it reads nothing the kernels before it
+// in the same call write, and those began after everything earlier on the
+// stream had completed).
 // layout: 0, or 1 for the int8 pair kernel of two pols in its second
 // instantiation (six operand stages, no staged epilogue groups); ignored
 // elsewhere.
