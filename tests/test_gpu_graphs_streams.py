@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import TOL_FP32, rel_frobenius_per_unit, to_numpy_int
+from helpers import TOL_FP32, rel_frobenius_per_unit, to_numpy_int, to_numpy_vis
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -110,3 +110,43 @@ def test_kernel_event_hook_brackets_the_main_launch(dtype, path):
     else:
         ref = oracle.correlate(x)
         assert rel_frobenius_per_unit(out.cpu().numpy().reshape(ref.shape), ref).max() < TOL_FP32
+
+
+@pytest.mark.parametrize("dtype,S,C,T", [("ci8", 150, 3, 1500), ("ci8", 64, 2, 256), ("cf16", 192, 5, 320)])
+def test_back_to_back_calls_read_the_preceding_kernels_writes(monkeypatch, dtype, S, C, T):
+    """The tensor path's launches are programmatic dependents of the kernel
+    before them on the stream. Each call here follows, with no
+    synchronisation, a copy kernel that rewrites its input, and precedes one
+    that copies its output away; small grids (2 channels of 64 stations)
+    leave most SMs free for an early start. Every call must see its own
+    input: int8 exact, f16 against the oracle. 150 and 192 stations (three
+    blocks) add the tail list's launches; 1500 int8 samples the power-checked
+    launch and its redo launch."""
+    from paper_1702_00844_gb300 import Plan
+    monkeypatch.setenv("CORR_TC_VARIANT", "pair")
+    g = synth.rng(91, S)
+    if dtype == "ci8":
+        xs = [synth.int8_normal(g, (C, S, T, 2)) for _ in range(3)]
+        xs[2] = np.where(g.random((C, S, T, 2, 2)) < 0.5, -127, 127).astype(np.int8)  # every tile redone
+    else:
+        xs = [synth.to_cf16(synth.complex_normal(g, (C, S, T, 2))) for _ in range(3)]
+    plan = Plan(S, C, T, dtype=dtype, path="tensor")
+    src = [torch.from_numpy(x).cuda() for x in xs]
+    x_dev = torch.empty_like(src[0])
+    out = plan.empty_out()
+    kept = []
+    order = [0, 1, 2, 1, 0, 2, 2, 0]
+    torch.cuda.synchronize()
+    for k in order:
+        x_dev.copy_(src[k])          # a kernel writing the input just before the call
+        plan.correlate(x_dev, out)
+        kept.append(out.clone())     # a kernel reading the output just after it
+    torch.cuda.synchronize()
+    plan.check_error()
+    for k, o in zip(order, kept):
+        if dtype == "ci8":
+            exact(o, xs[k])
+        else:
+            ref = oracle.correlate(xs[k], "cf16")
+            got = to_numpy_vis(o, "cf16").reshape(ref.shape)
+            assert rel_frobenius_per_unit(got, ref).max() < 1e-5
