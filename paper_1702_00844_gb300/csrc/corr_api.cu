@@ -171,7 +171,7 @@ corr_status_t encode_ig_map(CUtensorMap *m, const void *d_in, int S, int T, long
     }
     cuuint64_t dims[4] = {2 * (cuuint64_t)T, (cuuint64_t)S, (cuuint64_t)units, 1};
     cuuint64_t strides[3] = {(cuuint64_t)T * 16, (cuuint64_t)S * T * 16, (cuuint64_t)units * S * T * 16};
-    cuuint32_t box[4] = {2 * CORR_IG_BOX, 8, 1, 1};
+    cuuint32_t box[4] = {2 * CORR_IG_BOX, CORR_IG_KV / 4, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(d_in), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

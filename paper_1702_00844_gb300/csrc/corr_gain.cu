@@ -92,21 +92,26 @@ __global__ void sum_partials_kernel(const float *partial, int n, float *loss)
 __device__ __forceinline__ void store_w_tiles(float *at, int unit, int S, int c, int b, float2 v)
 {
     constexpr int PARTS = CORR_IG_A_FP32 ? 1 : 2;
-    const int mt = (2 * c) / 128, r = (2 * c) % 128, kb = (2 * b) / 32, kk = (2 * b) % 32;
+    constexpr int KV = CORR_IG_KV;   // floats per tile row
+    const int mt = (2 * c) / 128, r = (2 * c) % 128, kb = (2 * b) / KV, kk = (2 * b) % KV;
     const size_t tile = (((size_t)unit * ig_m_alloc(S) + mt) * ig_k_blocks(S) + kb) * PARTS;
-    const int q = kk >> 2;
+    const int q = kk >> 2;   // 16-byte chunk of the row
     const float vals[2][2] = {{v.x, -v.y}, {v.y, v.x}};   // rows r (re) and r + 1 (im)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int rr = r + h;
-        const size_t off = (size_t)rr * 32 + (size_t)((q ^ (rr & 7)) << 2) + (kk & 3);
+        // chunk q of row rr at 16-byte position q ^ (rr mod 8) (128-byte
+        // swizzle) or q ^ ((rr / 2) mod 4) (64-byte swizzle)
+        const int pos = KV == 32 ? (q ^ (rr & 7)) : (q ^ ((rr >> 1) & 3));
+        const size_t off = (size_t)rr * KV + (size_t)(pos << 2) + (kk & 3);
         const float a0 = vals[h][0], a1 = vals[h][1];
+        constexpr size_t TF = 128 * KV;   // floats per tile
         if (PARTS == 1) {
-            *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(a0, a1);
+            *reinterpret_cast<float2 *>(at + tile * TF + off) = make_float2(a0, a1);
         } else {
             const float h0 = tf32_round(a0), h1 = tf32_round(a1);
-            *reinterpret_cast<float2 *>(at + tile * 4096 + off) = make_float2(h0, h1);
-            *reinterpret_cast<float2 *>(at + (tile + 1) * 4096 + off) =
+            *reinterpret_cast<float2 *>(at + tile * TF + off) = make_float2(h0, h1);
+            *reinterpret_cast<float2 *>(at + (tile + 1) * TF + off) =
                 make_float2(tf32_round(a0 - h0), tf32_round(a1 - h1));
         }
     }

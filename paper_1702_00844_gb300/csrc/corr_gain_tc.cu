@@ -23,20 +23,22 @@
 // row tiles x 2 IG_N times on CTA pairs (a cluster of two, cta_group::2
 // MMAs of M = 256, N = 2 IG_N): each CTA stages its own row tile of A' and
 // its own IG_N times of the samples, so per SM the MMA does twice the work
-// for the same shared-memory operand traffic. Per K-block of 32 reduction
-// values (8 stations x 2 pols x re/im), through a ring of operand stages
-// that runs on across the CTA's tiles:
-//   - one thread issues the loads: A' as 16 KB bulk copies of tiles that
-//     the gain-gradient kernel wrote already swizzled, split into hi and lo
-//     (or in FP32 with CORR_IG_A_FP32, split here in shared memory), and the
-//     samples with TMA boxes of IG_BOX times (16 bytes each, 2 IG_BOX
-//     8-byte elements: one contiguous run) x 8 stations, landing
-//     station-major in the lo tile;
+// for the same shared-memory operand traffic. Per K-block of IG_KV = 32
+// reduction values (8 stations x 2 pols x re/im; 16 and 4 stations with
+// CORR_IG_KV = 16), through a ring of operand stages that runs on across
+// the CTA's tiles:
+//   - one thread issues the loads: A' as bulk copies (16 KB, or 8 KB) of
+//     tiles that the gain-gradient kernel wrote already swizzled, split into
+//     hi and lo (or in FP32 with CORR_IG_A_FP32, split here in shared
+//     memory), and the samples with TMA boxes of IG_BOX times (16 bytes
+//     each, 2 IG_BOX 8-byte elements: one contiguous run) x the K-block's
+//     stations, landing station-major in the lo tile;
 //   - IG_SW warps split the samples into hi and lo and transpose them into
-//     K-major rows (one time each) of 8 stations x 16 bytes, the chunk of
-//     station j in row t at 16-byte position j ^ (t mod 8): the 128-byte
-//     swizzled layout the MMA reads;
-//   - one thread (of the even CTA of a pair) issues 4 K-steps x 3 MMAs
+//     K-major rows (one time each) of the K-block's stations x 16 bytes, the
+//     chunk of station j in row t at 16-byte position j ^ (t mod 8): the
+//     128-byte swizzled layout the MMA reads (j ^ ((t / 2) mod 4), the
+//     64-byte one, with 16 values);
+//   - one thread (of the even CTA of a pair) issues IG_KV / 8 K-steps x 3 MMAs
 //     (K = 8) into one of two TMEM accumulators, alternating per tile; in a
 //     pair one thread of the odd CTA forwards each of its stages' "split
 //     done" phases to the even CTA with one cluster-scope arrival;
@@ -65,8 +67,12 @@ constexpr int IG_THREADS = 32 * (IG_MMA_WARP + 1);
 constexpr int IG_A_PARTS = CORR_IG_A_FP32 ? 1 : 2;   // A' tiles per K block in global memory
 constexpr int IG_M = 128, IG_N = CORR_IG_N;    // per CTA: rows of M' x times
 constexpr int IG_STAGES = CORR_IG_STAGES;
-constexpr uint32_t IG_A_BYTES = IG_M * 128;      // 16 KB: 128 rows x 32 tf32
-constexpr uint32_t IG_B_BYTES = IG_N * 128;      // IG_N rows x 32 tf32
+constexpr int IG_KV = CORR_IG_KV;                // reduction values per K-block
+constexpr int IG_KS = IG_KV / 4;                 // stations per K-block
+constexpr uint32_t IG_ROW = 4 * IG_KV;           // bytes per operand row: 128 or 64
+constexpr uint32_t IG_A_BYTES = IG_M * IG_ROW;   // 128 rows x IG_KV tf32
+constexpr uint32_t IG_B_BYTES = IG_N * IG_ROW;   // IG_N rows x IG_KV tf32
+static_assert(IG_KV == 16 || IG_KV == 32, "K-blocks of 16 or 32 reduction values");
 constexpr uint32_t IG_STAGE_BYTES = 2 * IG_A_BYTES + 2 * IG_B_BYTES;   // A hi, A lo, B hi, B lo
 constexpr uint32_t IG_EPI_BYTES = 4 * 32 * 17 * 4;                       // per-warp transpose
 constexpr int IG_BOX = CORR_IG_BOX;              // times per TMA box of samples
@@ -76,6 +82,18 @@ static_assert(IG_N % IG_BOX == 0 && 2 * IG_BOX <= 256, "a TMA box row holds at m
 // MMA width, TMEM columns (two accumulators) of a CTA
 template <bool PAIR> constexpr int ig_mma_n() { return PAIR ? 2 * IG_N : IG_N; }
 template <bool PAIR> constexpr uint32_t ig_tmem_cols() { return 2 * ig_mma_n<PAIR>(); }
+
+// Operand descriptors and the swizzled position of 16-byte chunk c of row r:
+// the 128-byte swizzle (c ^ (r mod 8)) for 32 values per row, the 64-byte
+// swizzle (c ^ ((r / 2) mod 4)) for 16.
+__device__ __forceinline__ uint64_t ig_desc(uint32_t saddr)
+{
+    return IG_KV == 32 ? smem_desc_sw128(saddr) : smem_desc_sw64(saddr);
+}
+__device__ __forceinline__ uint32_t ig_swz(int r, int c)
+{
+    return (uint32_t)(r * (int)IG_ROW + (IG_KV == 32 ? (c ^ (r & 7)) : (c ^ ((r >> 1) & 3))) * 16);
+}
 
 struct IgBars {
     uint64_t raw[IG_STAGES];     // loads landed (transaction bytes)
@@ -196,14 +214,14 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                     if (IG_A_PARTS == 2)
                         bulk_load_g2s(a_lo(s), a_tiles + ((size_t)kb * 2 + 1) * IG_A_BYTES, IG_A_BYTES,
                                       &bars->raw[s]);
-                    // the 8 stations of this K block, IG_N times from this
+                    // the IG_KS stations of this K block, IG_N times from this
                     // CTA's first (zero outside), into the lo tile: boxes of
                     // IG_BOX times, each landing station-major
 #pragma unroll
                     for (int h = 0; h < IG_N / IG_BOX; ++h)
                         tma_load_4d(smem + (size_t)s * IG_STAGE_BYTES + 2 * IG_A_BYTES + IG_B_BYTES +
-                                        (size_t)h * IG_BOX * 128,
-                                    &xmap, &bars->raw[s], 2 * (tl.t0 + h * IG_BOX), kb * 8, tl.unit, 0);
+                                        (size_t)h * IG_BOX * IG_KS * 16,
+                                    &xmap, &bars->raw[s], 2 * (tl.t0 + h * IG_BOX), kb * IG_KS, tl.unit, 0);
                 }
             }
             // on a give-up, let the copies in flight land before the CTA (and
@@ -234,7 +252,7 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                 // threads read consecutive times of one station. Once all
                 // split threads hold their chunks (rd), each writes hi and lo
                 // into row t at 16-byte position (station ^ (t mod 8)).
-                constexpr int CH = IG_N * 8 / IG_SPLIT_THREADS;   // chunks per thread
+                constexpr int CH = IG_N * IG_KS / IG_SPLIT_THREADS;   // chunks per thread
                 uint4 v[CH];
 #pragma unroll
                 for (int q = 0; q < CH; ++q)
@@ -265,8 +283,8 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
 #pragma unroll
                 for (int q = 0; q < CH; ++q) {
                     // box h = i / (8 IG_BOX), station, time h IG_BOX + i % IG_BOX
-                    const int i = q * IG_SPLIT_THREADS + pt, st = (i / IG_BOX) % 8,
-                              t = (i / (8 * IG_BOX)) * IG_BOX + i % IG_BOX;
+                    const int i = q * IG_SPLIT_THREADS + pt, st = (i / IG_BOX) % IG_KS,
+                              t = (i / (IG_KS * IG_BOX)) * IG_BOX + i % IG_BOX;
                     const float4 f = make_float4(__uint_as_float(v[q].x), __uint_as_float(v[q].y),
                                                  __uint_as_float(v[q].z), __uint_as_float(v[q].w));
                     const float4 hf =
@@ -276,7 +294,7 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                     // lo: the exact remainder, of which the MMA uses the tf32 bits
                     const uint4 l = make_uint4(__float_as_uint(f.x - hf.x), __float_as_uint(f.y - hf.y),
                                                __float_as_uint(f.z - hf.z), __float_as_uint(f.w - hf.w));
-                    const uint32_t sw = (uint32_t)(t * 128 + ((st ^ (t & 7)) * 16));
+                    const uint32_t sw = ig_swz(t, st);
                     sts128(b_hi(s) + sw, h);
                     sts128(b_lo(s) + sw, l);
                 }
@@ -370,11 +388,11 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
+                    for (int ks = 0; ks < IG_KV / 8; ++ks) {
                         const uint32_t o = 32u * ks;   // 8 tf32 of K per step
-                        mma(acc, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_hi(s) + o), (kb | ks) ? 1u : 0u);
-                        mma(acc, smem_desc_sw128(a_hi(s) + o), smem_desc_sw128(b_lo(s) + o), 1u);
-                        mma(acc, smem_desc_sw128(a_lo(s) + o), smem_desc_sw128(b_hi(s) + o), 1u);
+                        mma(acc, ig_desc(a_hi(s) + o), ig_desc(b_hi(s) + o), (kb | ks) ? 1u : 0u);
+                        mma(acc, ig_desc(a_hi(s) + o), ig_desc(b_lo(s) + o), 1u);
+                        mma(acc, ig_desc(a_lo(s) + o), ig_desc(b_hi(s) + o), 1u);
                     }
                     commit(&bars->empty[s]);
                 }

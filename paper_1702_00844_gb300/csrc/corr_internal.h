@@ -43,9 +43,9 @@ cudaError_t gain_loss_launch(const float2 *R, const float2 *g, const float2 *M, 
 // input gradient, from the same residuals.
 // Input gradient on the tensor cores (corr_gain_tc.cu): A' tiles written
 // by gain_grad_launch in tile mode, samples through a TMA map of boxes of
-// 4 floats x 8 stations x 256 times (128-byte swizzle).
+// 4 floats x CORR_IG_KV / 4 stations x up to 128 times.
 struct IgParams {
-    const float *at;          // A' tiles [unit][m tile][k block]([hi, lo] unless CORR_IG_A_FP32)[128 x 32 floats]
+    const float *at;          // A' tiles [unit][m tile][k block]([hi, lo] unless CORR_IG_A_FP32)[128 x CORR_IG_KV floats]
     float2 *gx;               // [unit][S][T][2] complex
     int S, T, units, m_tiles, k_blocks;
     int m_alloc;              // row tiles per unit in the A' buffer (m_tiles rounded up to even)
@@ -58,8 +58,16 @@ struct IgParams {
 #ifndef CORR_IG_N
 #define CORR_IG_N 128
 #endif
+// Reduction values (re and im of a station's two pols: 4 per station) per
+// K-block: 32 (rows of 128 bytes of tf32 in the 128-byte swizzled layout, 8
+// stations) or 16 (rows of 64 bytes in the 64-byte swizzled layout, 4
+// stations: stages half as large, twice as many in flight; measured slower,
+// the kernel's cost is per K-block rather than per byte in flight).
+#ifndef CORR_IG_KV
+#define CORR_IG_KV 32
+#endif
 #ifndef CORR_IG_STAGES
-#define CORR_IG_STAGES 3
+#define CORR_IG_STAGES (CORR_IG_KV == 16 ? 6 : 3)
 #endif
 #define CORR_IG_BOX (CORR_IG_N < 128 ? CORR_IG_N : 128)
 // Warps that split the operands into tf32 hi and lo.
@@ -86,15 +94,16 @@ struct TfParams {
 };
 cudaError_t tf32_correlate_launch(const void *xmap, const TfParams &p, cudaStream_t s);
 
-// Row tiles (128 rows of M' = 4S) and K blocks (32 of K' = 4S) of the tiles.
+// Row tiles (128 rows of M' = 4S) and K blocks (CORR_IG_KV of K' = 4S) of
+// the tiles.
 __host__ __device__ inline int ig_m_tiles(int S) { return (4 * S + 127) / 128; }
-__host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + 31) / 32; }
+__host__ __device__ inline int ig_k_blocks(int S) { return (4 * S + CORR_IG_KV - 1) / CORR_IG_KV; }
 // A CTA pair takes two row tiles; with an odd count the second of the last
 // pair reads a zero tile.
 __host__ __device__ inline int ig_m_alloc(int S) { return (ig_m_tiles(S) + 1) & ~1; }
 inline size_t ig_tile_bytes(int S, long long units)
 {
-    return (size_t)units * ig_m_alloc(S) * ig_k_blocks(S) * (CORR_IG_A_FP32 ? 1 : 2) * 16384;
+    return (size_t)units * ig_m_alloc(S) * ig_k_blocks(S) * (CORR_IG_A_FP32 ? 1 : 2) * (128 * 4 * CORR_IG_KV);
 }
 // pair: tiles of two row tiles on CTA pairs (cta_group::2)
 cudaError_t input_grad_tc_launch(const void *xmap, const IgParams &p, cudaStream_t s, bool pair);
