@@ -83,6 +83,20 @@ static_assert(IG_N % IG_BOX == 0 && 2 * IG_BOX <= 256, "a TMA box row holds at m
 template <bool PAIR> constexpr int ig_mma_n() { return PAIR ? 2 * IG_N : IG_N; }
 template <bool PAIR> constexpr uint32_t ig_tmem_cols() { return 2 * ig_mma_n<PAIR>(); }
 
+// Shared-memory descriptor of a K-major operand tile in the 64-byte swizzled
+// layout (as smem_desc_sw128 in ptx.cuh, for rows of 64 bytes): 8-row groups
+// 512 bytes apart, layout 4, tile base 512-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
 // Operand descriptors and the swizzled position of 16-byte chunk c of row r:
 // the 128-byte swizzle (c ^ (r mod 8)) for 32 values per row, the 64-byte
 // swizzle (c ^ ((r / 2) mod 4)) for 16.
@@ -374,14 +388,14 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
             bool ok = true;
             for (int i = 0; i < my_tiles && ok; ++i) {
                 const int b = i & 1;
-                if (i >= 2 && !mbar_wait_bounded(&bars->acc_empty[b], (uint32_t)((i >> 1) - 1) & 1, abort_flag,
+                if (i >= 2 && !mbar_wait_bounded<PAIR>(&bars->acc_empty[b], (uint32_t)((i >> 1) - 1) & 1, abort_flag,
                                                  p.err, p.wait_ns))
                     break;
                 tc_fence_after();
                 const uint32_t acc = tmem + (uint32_t)(b * MN);
                 for (int kb = 0; kb < KB; ++kb, ++g) {
                     const int s = (int)(g % IG_STAGES);
-                    if (!mbar_wait_bounded(&bars->full[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err,
+                    if (!mbar_wait_bounded<PAIR>(&bars->full[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err,
                                            p.wait_ns)) {
                         ok = false;
                         break;

@@ -447,19 +447,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
     return d;
 }
 
-// The same for the 64-byte swizzled layout: rows of 64 bytes, 8-row groups
-// 512 bytes apart, layout 4; tile base 512-byte aligned.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(16u >> 4) << 16;
-    d |= (uint64_t)(512u >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
-    return d;
-}
-
 // Instruction descriptor of kind::f16 with f16 A and B, f32 accumulator,
 // both operands K-major.
 //   bits 4-5 D format (1 = f32)  bits 7-9 A format (0 = f16)
