@@ -256,7 +256,11 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
         for (int i = 0; i < my_tiles && ok; ++i) {
             for (int kb = 0; kb < KB; ++kb, ++g) {
                 const int s = (int)(g % IG_STAGES);
-                if (!mbar_wait_bounded(&bars->raw[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
+                // each wait's outcome is taken by the whole warp, so that a
+                // warp leaves together and its lanes meet again below
+                const bool landed =
+                    mbar_wait_bounded(&bars->raw[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns);
+                if (!__all_sync(0xffffffffu, landed)) {
                     ok = false;
                     break;
                 }
@@ -290,7 +294,9 @@ __device__ __forceinline__ void ig_body(const CUtensorMap &xmap, const IgParams 
                                                      __float_as_uint(tf32_round(f.z - hf.z)),
                                                      __float_as_uint(tf32_round(f.w - hf.w))));
                 }
-                if (!mbar_wait_bounded(&bars->rd[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns)) {
+                const bool read =
+                    mbar_wait_bounded(&bars->rd[s], (uint32_t)(g / IG_STAGES) & 1, abort_flag, p.err, p.wait_ns);
+                if (!__all_sync(0xffffffffu, read)) {
                     ok = false;
                     break;
                 }
