@@ -652,8 +652,9 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
         return;
     }
 
-    // In a pair, the even CTA's full and acc_empty barriers also count one
-    // arrival of the odd CTA's relay thread (see the relay below).
+    // In a pair, the even CTA's full barriers also count one arrival of the
+    // odd CTA's relay thread (see the relay below), and its acc_empty
+    // barriers one arrival of each of the odd CTA's four epilogue warps.
     const uint32_t relay = PAIR && leader ? 1u : 0u;
     if (tid == 0) {
         for (int s = 0; s < OPS; ++s) {
@@ -662,7 +663,7 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars->acc_full[b], 1);
-            mbar_init(&bars->acc_empty[b], N_EPILOGUE + relay);
+            mbar_init(&bars->acc_empty[b], N_EPILOGUE + 4 * relay);
         }
         mbar_init(&bars->fin, 1);
         bars->abort_flag = 0;
@@ -869,12 +870,28 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
             const long long unit_off = (long long)item.unit * P.out_unit_elems + (NPOL == 1 ? 0 : p1 * 2);
             for (int c = 0; c < nch; ++c, ++acc_it) {
                 const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
-                if (!mbar_wait_bounded(&bars->acc_full[buf], ap, abort_flag, p.err, p.wait_ns)) {
+                // the warp takes the wait's outcome together: its TMEM loads
+                // and its release below are warp-wide
+                const bool got = mbar_wait_bounded(&bars->acc_full[buf], ap, abort_flag, p.err, p.wait_ns);
+                if (!__all_sync(0xffffffffu, got)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + buf * BUFCOLS + ((uint32_t)(eq * 32) << 16);
+                // Every column of this chunk has been read: the next chunk's
+                // MMAs may overwrite the accumulator. In a pair the odd CTA's
+                // warps arrive on the even CTA's barrier, where the MMAs are
+                // issued, one cluster-scope arrival per warp.
+                auto release_acc = [&]() {
+                    tc_fence_before();
+                    if (PAIR && !leader) {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&bars->acc_empty[buf]), 0));
+                    } else {
+                        mbar_arrive(&bars->acc_empty[buf]);
+                    }
+                };
                 const bool last = c == nch - 1;
                 // Column groups of 16 TMEM columns (8 column stations x 2 pols),
                 // Re and Im. The first ndirect groups are stored to global
@@ -903,8 +920,7 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
                     store_group<DT, NPOL>(P, unit_off, s1, item.cb0 * TC_RS + cc * 8, c > 0, last, ra, ia);
                     tmem_wait_ld();
                     if (nst == 0 && cc + 2 >= ndirect) {  // every column of this chunk has been read
-                        tc_fence_before();
-                        mbar_arrive(&bars->acc_empty[buf]);
+                        release_acc();
                         released = true;
                     }
                     if (has1) {
@@ -936,8 +952,7 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
                                 sts128(slot + j * 512, make_uint4(vr[2 * j], vi[2 * j], vr[2 * j + 1], vi[2 * j + 1]));
                         };
                         auto release = [&]() {  // every column of this chunk has been read
-                            tc_fence_before();
-                            mbar_arrive(&bars->acc_empty[buf]);
+                            release_acc();
                             released = true;
                         };
                         tmem_ld_32x32b_x16(taddr + ndirect * 16, ra);
@@ -984,10 +999,7 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
                         }
                     }
                 }
-                if (!released) {
-                    tc_fence_before();
-                    mbar_arrive(&bars->acc_empty[buf]);
-                }
+                if (!released) release_acc();
             }
         }
     } else if (leader) {
@@ -1084,45 +1096,32 @@ template <int DT, int V, int NPOL, int LY = 0> __device__ __forceinline__ void t
         mbar_wait_bounded(&bars->fin, 0, &dummy_abort, p.err, 2000000000ull);
     } else if constexpr (PAIR) {
         // ------------------------------------------ relay (odd CTA of a pair)
-        // This CTA's producers and epilogue arrive on its own barriers (CTA
-        // scope, as in a single CTA: a cluster-scope release in every
-        // producer thread would also wait for its asynchronous copies in
-        // flight). One thread follows the MMA thread's order of waits and
-        // forwards each completed phase to the even CTA with one
-        // cluster-scope arrival: the K-blocks of a chunk, then the release
-        // of the accumulator after this CTA's epilogue has read it.
+        // This CTA's producers arrive on its own "full" barriers (CTA scope,
+        // as in a single CTA: a cluster-scope release in every producer
+        // thread would also wait for its asynchronous copies in flight). One
+        // thread forwards each completed phase, in the MMA thread's order of
+        // K-blocks, to the even CTA with one cluster-scope arrival. It never
+        // waits for the accumulator (the epilogue warps release it
+        // themselves), so the next tile's first K-blocks reach the even CTA
+        // while this tile's accumulator is still being read.
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t acc_it = 0;
             bool ok = true;
             for (int it = item0; it < n_items && ok; it += item_step) {
                 const Item item = get_item(p, it);
                 const TcProblem P = get_prob(p, item.prob);
                 const int nkb = (P.T + TC_KB_T - 1) / TC_KB_T;
-                const int nch = n_chunks(nkb, p.chunk_kb);
-                const int ckb = p.chunk_kb > 0 ? p.chunk_kb : nkb;
-                for (int c = 0; c < nch && ok; ++c, ++acc_it) {
-                    const int kb_lo = c * ckb;
-                    const int kb_hi = min(nkb, kb_lo + ckb);
-                    for (int kb = kb_lo; kb < kb_hi; ++kb) {
-                        if (!mbar_wait_bounded(&bars->full[stage], phase, abort_flag, p.err, p.wait_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_arrive_cluster(mapa_shared(smem_u32(&bars->full[stage]), 0));
-                        if (++stage == OPS) {
-                            stage = 0;
-                            phase ^= 1;
-                        }
-                    }
-                    if (!ok) break;
-                    const uint32_t buf = acc_it % NBUF, ap = (acc_it / NBUF) & 1;
-                    if (!mbar_wait_bounded(&bars->acc_empty[buf], ap, abort_flag, p.err, p.wait_ns)) {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait_bounded(&bars->full[stage], phase, abort_flag, p.err, p.wait_ns)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars->acc_empty[buf]), 0));
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars->full[stage]), 0));
+                    if (++stage == OPS) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
                 }
             }
         }
