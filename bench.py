@@ -606,6 +606,24 @@ def secondary(x8, torch):
                                                   "variant": p1.tile_variant()}
     del p1, o1
     torch.cuda.empty_cache()
+    # the first 120 channels' bytes read as 30 channels of 1024 stations (the
+    # same correlator ops as the 256-station workload): the tile triangle's
+    # diagonal blocks weigh less (524800 of the 589824 station pairs the pair
+    # tiles compute are needed, against 32896 of 49152 at 256 stations)
+    Sw, Cw = 4 * S3, C3 // 16
+    pw = Plan(Sw, Cw, T3, dtype="ci8", path="tensor")
+    xw = x8[: Cw * Sw // S3].view(Cw, Sw, T3, 2, 2)
+    ow = pw.empty_out()
+    ms = time_launches(lambda: pw.correlate(xw, ow), 10, 3, st)
+    opsw = ops_of(Sw, T3, Cw)
+    pk, _ = measured_peaks()
+    res["tensor_int8_1024_stations"] = {
+        "ms": ms, "TOPS": opsw / ms / 1e9,
+        "frac": opsw / ms / 1e9 / float(pk.get("bf16_tflops", 1893.4)),
+        "useful_fraction": (Sw * (Sw + 1) / 2) / (((Sw // 64) // 2) * ((Sw // 64) // 2 + 1) / 2 * 4 * 4096),
+        "variant": pw.tile_variant()}
+    del pw, ow
+    torch.cuda.empty_cache()
     # sample layouts (corr_reorder) on the int8 precision samples: the
     # time-major layout of Section 4.4 and the per-station streams before the
     # corner turn of Section 7, each into the correlator's layout. HBM-bound:
