@@ -77,7 +77,7 @@ template <int DT> struct RawBytes { static constexpr int value = DT == 1 ? 64 : 
 #define CORR_TC_RAW_I8 5
 #endif
 #ifndef CORR_TC_OPS_PAIR_F16
-#define CORR_TC_OPS_PAIR_F16 4
+#define CORR_TC_OPS_PAIR_F16 5
 #endif
 #ifndef CORR_TC_RAW_PAIR_F16
 #define CORR_TC_RAW_PAIR_F16 2
